@@ -1,0 +1,80 @@
+"""FP64 CPU oracle for the segmented DFT (test infrastructure only).
+
+Only tests/, ``__graft_entry__.smoke()`` and the CPU-baseline leg of bench.py
+may import this package.  The product library never calls it and there is no
+CPU fallback built on it.
+
+What it computes (paper Sec. III, segments as <offset, FFT segment> records;
+Sec. I, Cooley-Tukey = the DFT): for each segment s of length n,
+
+    X_s[k] = scale * sum_j x_s[j] * exp(sigma * 2 pi i j k / n)
+
+with sigma = -1 forward / +1 inverse and scale 1 (NONE), 1/n on the inverse
+(BACKWARD) or 1/sqrt(n) (ORTHO).  The arithmetic is the recursive radix-2
+FFT in oracle.c, in double precision.  The power output is |X|^2 in double.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FORWARD = -1
+INVERSE = +1
+NORM_NONE = 0
+NORM_BACKWARD = 1
+NORM_ORTHO = 2
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        for name, ptr_t in (("oracle_fft_c64", ctypes.c_void_p), ("oracle_fft_c128", ctypes.c_void_p)):
+            fn = getattr(lib, name)
+            fn.restype = ctypes.c_int
+            fn.argtypes = [ptr_t, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def fft(x, direction: int = FORWARD, norm: int = NORM_NONE, nthreads: int = None) -> np.ndarray:
+    """Segment-wise DFT of ``x`` along its last axis (length n, a power of two).
+
+    ``x`` may be complex64 (the library's sample type; widened to double
+    inside) or complex128 (exact inputs for pinning).  Returns complex128 of
+    the same shape.
+    """
+    lib = _load()
+    x = np.asarray(x)
+    if x.dtype not in (np.complex64, np.complex128):
+        raise TypeError("oracle.fft wants complex64 or complex128 input")
+    if x.ndim == 0:
+        raise ValueError("oracle.fft wants at least one axis")
+    n = x.shape[-1]
+    nseg = int(np.prod(x.shape[:-1], dtype=np.int64)) if x.ndim > 1 else 1
+    xc = np.ascontiguousarray(x)
+    out = np.empty(x.shape, dtype=np.complex128)
+    if nseg == 0 or n == 0:
+        return out
+    fn = lib.oracle_fft_c64 if xc.dtype == np.complex64 else lib.oracle_fft_c128
+    rc = fn(xc.ctypes.data, out.ctypes.data, n, nseg, int(direction), int(norm),
+            int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments (status %d): n=%d must be a power of two" % (rc, n))
+    return out
+
+
+def power(x, direction: int = FORWARD, norm: int = NORM_NONE, nthreads: int = None) -> np.ndarray:
+    """|X|^2 of the segment-wise DFT, in double."""
+    X = fft(x, direction, norm, nthreads)
+    return X.real * X.real + X.imag * X.imag
