@@ -1,0 +1,186 @@
+/*
+ * fftseg — batched forward/inverse complex FFTs over fixed-length,
+ * offset-tagged segments of a very large signal, on one GB300 (sm_103a).
+ *
+ * The operation (paper Sec. III): a signal file is cut into <offset, FFT
+ * segment> records; segment s holds samples [s*n, (s+1)*n) and starts at byte
+ * offset s*n*8 of the complex64 signal; every segment is transformed on its
+ * own (a batched plan partitions the segments in memory) and the outputs are
+ * kept in positional order.  The transform is the Cooley-Tukey FFT (Sec. I),
+ * i.e. for every segment
+ *
+ *     X_s[k] = scale * sum_{j<n} x_s[j] * exp(sigma * 2 pi i * j*k / n)
+ *
+ * sigma = -1 (FFTSEG_FORWARD) or +1 (FFTSEG_INVERSE); scale = 1 (NORM_NONE),
+ * 1/n on the inverse (NORM_BACKWARD) or 1/sqrt(n) (NORM_ORTHO).  Bins are in
+ * natural order k = 0..n-1.  The paper leaves the sign and the scaling open;
+ * these are the conventions of the FFT library it calls.
+ *
+ * Data layout: complex64 = interleaved {float re, float im}, 8 bytes; a batch
+ * is [batch][n] contiguous.  Power output (FFTSEG_OUT_POWER) is float32
+ * |X|^2, [batch][n] contiguous.  Device buffers must be 16-byte aligned.
+ *
+ * Ownership: the caller owns every buffer it passes (device or host) and the
+ * CUDA stream.  The library owns plans (twiddle tables, workspace) and the
+ * pinned staging, streams and events it creates inside fftseg_stream and the
+ * server.
+ *
+ * Errors: every entry point returns an fftseg_status; nothing throws or exits
+ * across this boundary.  fftseg_last_error() returns a message for the last
+ * failing call on the calling thread.  Asynchronous entry points report launch
+ * errors; faults inside kernels surface on the caller's next synchronisation.
+ *
+ * There is no CPU fallback: every transform runs in this library's own
+ * sm_103a kernels.
+ */
+#ifndef FFTSEG_H
+#define FFTSEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *fftseg_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+    FFTSEG_OK = 0,
+    FFTSEG_E_INVALID = -1,     /* bad argument (null, misaligned, out of range) */
+    FFTSEG_E_NOMEM = -2,       /* device or pinned allocation failed */
+    FFTSEG_E_CUDA = -3,        /* a CUDA runtime call or launch failed */
+    FFTSEG_E_IO = -4,          /* a reader or writer callback failed */
+    FFTSEG_E_PARTIAL = -5,     /* the signal ends inside a segment and zero padding is off */
+    FFTSEG_E_TIMEOUT = -6,     /* a bounded wait ran out (server poll, device wait) */
+    FFTSEG_E_UNSUPPORTED = -7  /* n not a power of two in [2, 2^24], or a precision/size mix not built */
+} fftseg_status;
+
+enum { FFTSEG_FORWARD = -1, FFTSEG_INVERSE = +1 };
+enum { FFTSEG_NORM_NONE = 0, FFTSEG_NORM_BACKWARD = 1, FFTSEG_NORM_ORTHO = 2 };
+enum { FFTSEG_PREC_FP32 = 0, FFTSEG_PREC_TC_FP16 = 1, FFTSEG_PREC_TC_BF16 = 2 };
+enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
+
+/* plan flags */
+#define FFTSEG_FLAG_ZERO_PAD 0x1u     /* fftseg_stream: zero-pad a trailing partial segment */
+#define FFTSEG_FLAG_FORCE_TWOPASS 0x2u /* use the two-pass four-step path even where one pass fits */
+/* single-pass cluster path: request a cluster of 2^c CTAs (0 = the library's choice) */
+#define FFTSEG_FLAG_CLUSTER_LOG2(c) (((unsigned)(c) & 0xFu) << 8)
+
+#define FFTSEG_MAX_LOG2N 24
+
+typedef struct fftseg_plan_s *fftseg_plan;
+
+/*
+ * Create a plan for `batch` segments of n points (Sec. III: one batched plan
+ * over a block of segments).  Twiddle tables are evaluated in double
+ * precision on the host and rounded once to float32 (split into hi+lo halves
+ * for the tensor-core precisions); they stay resident on the current device.
+ *   n          power of two, 2 <= n <= 2^24, else FFTSEG_E_UNSUPPORTED
+ *   batch      >= 1: the most segments one fftseg_exec call processes
+ *   direction  FFTSEG_FORWARD or FFTSEG_INVERSE
+ *   norm       FFTSEG_NORM_*
+ *   precision  FFTSEG_PREC_FP32, or a tensor-core radix-16 precision
+ *              (n must be a power of 16 from 16^3 to 16^6)
+ *   out_kind   FFTSEG_OUT_COMPLEX or FFTSEG_OUT_POWER
+ * On success *out owns device memory until fftseg_plan_destroy.
+ */
+int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm,
+                       int precision, int out_kind, unsigned flags);
+
+/*
+ * Transform `batch` segments: d_in [batch][n] complex64 -> d_out [batch][n]
+ * (complex64, or float32 for the power output).  d_in == d_out transforms in
+ * place (complex output only).  Asynchronous on `stream`.  Device pointers,
+ * 16-byte aligned.
+ */
+int fftseg_exec(fftseg_plan p, const void *d_in, void *d_out, fftseg_stream_t stream);
+
+/* As fftseg_exec for the first `nseg` (0 <= nseg <= batch) segments. */
+int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg,
+                  fftseg_stream_t stream);
+
+/*
+ * Streaming chunker (Sec. III's split/transform/merge on one GPU; the paper's
+ * per-block single allocate + copy becomes a pinned, double-buffered host
+ * link): reads the signal from byte `start_offset` to `total_bytes` in chunks
+ * of `chunk_segments` segments (<= the plan's batch), copies each chunk to the
+ * device on one stream, transforms it on a second and copies the result back
+ * on a third, and hands every result block to the writer at its output byte
+ * offset (s*n*8 for complex output, s*n*4 for power output), in offset order.
+ *   rd(ctx, byte_offset, dst, bytes) fills dst (pinned host memory) and
+ *      returns the bytes read (a short read ends the signal) or < 0 on error.
+ *   wr(ctx, byte_offset, src, bytes) consumes a result block, returns 0 or < 0.
+ *   start_offset  must be a multiple of n*8 (resume point).
+ *   committed_offset  receives the input byte offset up to which every output
+ *      has been handed to the writer (resume from there after an error).
+ * Synchronous.  Returns FFTSEG_E_IO on a callback error, FFTSEG_E_PARTIAL if
+ * the signal ends inside a segment without FFTSEG_FLAG_ZERO_PAD (the complete
+ * segments before it are written).
+ */
+typedef int64_t (*fftseg_read_fn)(void *ctx, int64_t byte_offset, void *dst, int64_t bytes);
+typedef int (*fftseg_write_fn)(void *ctx, int64_t byte_offset, const void *src, int64_t bytes);
+int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn wr, void *wctx,
+                  int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
+                  int64_t *committed_offset);
+
+/* Phase split of the last fftseg_stream call on this plan, in milliseconds
+ * (the analog of the paper's I/O versus FFT breakdown, Sec. IV Figs. 4-5):
+ * out[0] read callback, out[1] H2D, out[2] transform, out[3] D2H,
+ * out[4] write callback, out[5] wall time. */
+int fftseg_stream_phases(fftseg_plan p, double out[6]);
+
+int fftseg_plan_destroy(fftseg_plan p);
+
+/* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core),
+ * info[1] n1, info[2] n2, info[3] workspace bytes, info[4] segments per
+ * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
+int fftseg_plan_info(fftseg_plan p, int64_t info[6]);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *fftseg_last_error(void);
+
+/* Number of kernels this library has launched in this process. */
+int64_t fftseg_launch_count(void);
+
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of segment-FFT jobs of different lengths.  Jobs are
+ * admitted while the bytes they touch fit the HBM budget and fewer than
+ * max_inflight_jobs run; admitted jobs are grouped by length, and each group
+ * runs in one persistent ragged kernel launch (replayed from a captured CUDA
+ * graph per length bucket) on the server's stream.  Plans and twiddles stay
+ * resident.  A job's result is the same alone and in any mix.
+ */
+typedef struct fftsrv_s *fftsrv;
+typedef struct {
+    int64_t hbm_budget_bytes; /* bytes of job input+output that may be in flight */
+    int max_inflight_jobs;
+    fftseg_stream_t stream;   /* NULL: the server creates its own stream */
+} fftsrv_config;
+typedef struct {
+    const void *d_in; /* [nseg][n] complex64, device */
+    void *d_out;      /* [nseg][n] complex64, device (may equal d_in) */
+    int64_t n;        /* power of two, 2^1..2^22 */
+    int64_t nseg;     /* >= 1 */
+    int direction;
+    int norm;
+} fftsrv_job;
+
+int fftsrv_create(fftsrv *out, const fftsrv_config *cfg);
+/* Queue a job (non-blocking).  *job_id identifies it for fftsrv_poll. */
+int fftsrv_submit(fftsrv s, const fftsrv_job *job, uint64_t *job_id);
+/* Wait up to timeout_us (0 = just check) for the job.  Returns FFTSEG_OK with
+ * *job_status = the job's final status once it has completed, or
+ * FFTSEG_E_TIMEOUT while it is still queued or running. */
+int fftsrv_poll(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status);
+/* Server counters: out[0] jobs submitted, out[1] completed, out[2] launches,
+ * out[3] peak admitted bytes, out[4] queue depth now. */
+int fftsrv_stats(fftsrv s, int64_t out[5]);
+/* Drain every queued job, then release the server. */
+int fftsrv_destroy(fftsrv s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FFTSEG_H */

@@ -1,0 +1,257 @@
+"""fftseg: batched forward/inverse complex FFTs over fixed-length segments of a
+very large signal, on one GB300 (sm_103a).
+
+Thin ctypes binding of the C ABI in include/fftseg.h: it marshals arguments
+(torch tensors -> device pointers, torch streams -> cudaStream_t) and does no
+arithmetic.  Every transform runs in libfftseg.so's CUDA kernels; if that
+library is missing or cannot load, importing the binding's entry points raises
+(there is no CPU fallback).
+
+Paper: Tsiomenko & Rees, "Accelerating Fast Fourier Transforms Using Hadoop
+and CUDA", Sec. III (segments as <offset, FFT segment> records, batched plan
+over a block, outputs in positional order).
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfftseg.so")
+
+FORWARD, INVERSE = -1, 1
+NORM_NONE, NORM_BACKWARD, NORM_ORTHO = 0, 1, 2
+PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
+OUT_COMPLEX, OUT_POWER = 0, 1
+FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS = 0x1, 0x2
+
+
+PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core"}
+
+OK, E_INVALID, E_NOMEM, E_CUDA, E_IO, E_PARTIAL, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+
+
+def FLAG_CLUSTER_LOG2(c):
+    """Plan flag: single-pass cluster of 2^c CTAs (0 = the library's choice)."""
+    return (int(c) & 0xF) << 8
+
+
+STATUS_NAMES = {0: "OK", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA", -4: "E_IO", -5: "E_PARTIAL",
+                -6: "E_TIMEOUT", -7: "E_UNSUPPORTED"}
+
+READ_FN = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64)
+WRITE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64)
+
+
+class FFTSegError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%s)" % (message, STATUS_NAMES.get(status, status)))
+        self.status = status
+
+
+class SrvConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight_jobs", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
+
+
+class SrvJob(ctypes.Structure):
+    _fields_ = [("d_in", ctypes.c_void_p), ("d_out", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("nseg", ctypes.c_int64), ("direction", ctypes.c_int), ("norm", ctypes.c_int)]
+
+
+_lib = None
+
+_SIGS = {
+    "fftseg_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "fftseg_exec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "fftseg_exec_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                     ctypes.c_void_p]),
+    "fftseg_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.POINTER(ctypes.c_int64)]),
+    "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "fftseg_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+    "fftseg_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "fftseg_last_error": (ctypes.c_char_p, []),
+    "fftseg_launch_count": (ctypes.c_int64, []),
+    "fftsrv_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(SrvConfig)]),
+    "fftsrv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvJob), ctypes.POINTER(ctypes.c_uint64)]),
+    "fftsrv_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+    "fftsrv_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "fftsrv_destroy": (ctypes.c_int, [ctypes.c_void_p]),
+}
+
+
+def lib():
+    """The loaded libfftseg.so.  Raises if it is absent: there is no fallback."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libfftseg.so is not built (run __graft_entry__.build()); "
+                               "fftseg has no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().fftseg_last_error().decode(errors="replace")
+
+
+def launch_count() -> int:
+    return int(lib().fftseg_launch_count())
+
+
+def check(status, what="fftseg"):
+    if status != OK:
+        raise FFTSegError(status, "%s: %s" % (what, last_error()))
+    return status
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+def segment_offset(s: int, n: int, sample_bytes: int = 8) -> int:
+    """Byte offset of segment s (Sec. III: offset = bytes from the start of the file)."""
+    return s * n * sample_bytes
+
+
+def segment_count(total_bytes: int, n: int, sample_bytes: int = 8):
+    """(complete segments, bytes left over) in a signal of total_bytes."""
+    seg = n * sample_bytes
+    return total_bytes // seg, total_bytes % seg
+
+
+class Plan:
+    """A batched plan over `batch` segments of n points (fftseg_plan_create)."""
+
+    def __init__(self, n, batch, direction=FORWARD, norm=NORM_NONE, precision=PREC_FP32,
+                 out_kind=OUT_COMPLEX, flags=0):
+        self._h = ctypes.c_void_p()
+        self.n, self.batch, self.direction, self.norm = int(n), int(batch), direction, norm
+        self.precision, self.out_kind, self.flags = precision, out_kind, flags
+        check(lib().fftseg_plan_create(ctypes.byref(self._h), self.n, self.batch, direction, norm,
+                                       precision, out_kind, flags), "fftseg_plan_create")
+
+    @property
+    def handle(self):
+        return self._h.value
+
+    def info(self) -> dict:
+        a = (ctypes.c_int64 * 6)()
+        check(lib().fftseg_plan_info(self._h, a), "fftseg_plan_info")
+        return {"path": PATH_NAMES.get(a[0], a[0]), "n1": a[1], "n2": a[2], "work_bytes": a[3],
+                "work_segs": a[4], "launches_per_exec": a[5]}
+
+    def exec_ptr(self, d_in: int, d_out: int, nseg: int = None, stream=None) -> None:
+        """Raw-pointer form of fftseg_exec_n (asynchronous on `stream`)."""
+        nseg = self.batch if nseg is None else nseg
+        check(lib().fftseg_exec_n(self._h, d_in, d_out, nseg, _stream_handle(stream)), "fftseg_exec")
+
+    def exec(self, x, out=None, nseg=None, stream=None):
+        """Transform the first nseg segments of the device tensor x (complex64,
+        contiguous, [.., n]); returns `out` (allocated if None)."""
+        import torch
+        if not (x.is_cuda and x.is_contiguous()):
+            raise ValueError("fftseg.Plan.exec wants a contiguous CUDA tensor")
+        if x.dtype != torch.complex64:
+            raise ValueError("fftseg.Plan.exec wants complex64 input")
+        nseg = (x.numel() // self.n) if nseg is None else nseg
+        if out is None:
+            dt = torch.float32 if self.out_kind == OUT_POWER else torch.complex64
+            out = torch.empty(x.shape, dtype=dt, device=x.device)
+        self.exec_ptr(x.data_ptr(), out.data_ptr(), nseg, stream)
+        return out
+
+    def stream(self, reader, rctx, writer, wctx, total_bytes, start_offset=0, chunk_segments=0):
+        """fftseg_stream.  reader/writer: C function pointers (int) with their
+        context pointers, or Python callables (ctx ignored).  Returns
+        (status, committed_offset) and does not raise on E_IO/E_PARTIAL."""
+        keep = []
+
+        def as_fn(f, proto):
+            if isinstance(f, int):
+                return ctypes.c_void_p(f)
+            cb = proto(f)
+            keep.append(cb)
+            return ctypes.cast(cb, ctypes.c_void_p)
+
+        committed = ctypes.c_int64(0)
+        rc = lib().fftseg_stream(self._h, as_fn(reader, READ_FN), rctx, as_fn(writer, WRITE_FN), wctx,
+                                 int(total_bytes), int(start_offset), int(chunk_segments),
+                                 ctypes.byref(committed))
+        if rc not in (OK, E_IO, E_PARTIAL):
+            check(rc, "fftseg_stream")
+        return rc, committed.value
+
+    def stream_phases(self) -> dict:
+        a = (ctypes.c_double * 6)()
+        check(lib().fftseg_stream_phases(self._h, a), "fftseg_stream_phases")
+        return dict(zip(("read_ms", "h2d_ms", "fft_ms", "d2h_ms", "write_ms", "wall_ms"), list(a)))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            lib().fftseg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching server (fftsrv_*)."""
+
+    def __init__(self, hbm_budget_bytes=32 << 30, max_inflight_jobs=64, stream=None):
+        self._h = ctypes.c_void_p()
+        cfg = SrvConfig(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight_jobs=int(max_inflight_jobs),
+                        stream=(None if stream is None else _stream_handle(stream)))
+        check(lib().fftsrv_create(ctypes.byref(self._h), ctypes.byref(cfg)), "fftsrv_create")
+
+    def submit(self, d_in, d_out, n, nseg, direction=FORWARD, norm=NORM_NONE) -> int:
+        job = SrvJob(d_in=_ptr(d_in), d_out=_ptr(d_out), n=int(n), nseg=int(nseg), direction=direction,
+                     norm=norm)
+        jid = ctypes.c_uint64()
+        check(lib().fftsrv_submit(self._h, ctypes.byref(job), ctypes.byref(jid)), "fftsrv_submit")
+        return jid.value
+
+    def poll(self, job_id, timeout_us=0):
+        """(done, job_status): done False while the job is queued or running."""
+        st = ctypes.c_int(0)
+        rc = lib().fftsrv_poll(self._h, job_id, int(timeout_us), ctypes.byref(st))
+        if rc == E_TIMEOUT:
+            return False, None
+        check(rc, "fftsrv_poll")
+        return True, st.value
+
+    def stats(self) -> dict:
+        a = (ctypes.c_int64 * 5)()
+        check(lib().fftsrv_stats(self._h, a), "fftsrv_stats")
+        return dict(zip(("submitted", "completed", "launches", "peak_admitted_bytes", "queue_depth"), list(a)))
+
+    def destroy(self):
+        if self._h and self._h.value:
+            rc = lib().fftsrv_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            check(rc, "fftsrv_destroy")
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

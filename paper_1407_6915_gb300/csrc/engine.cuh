@@ -1,0 +1,207 @@
+// Register/shared-memory FFT engine shared by the sm_103a kernels.
+//
+// A "tile" is W lines of L points each (L, W powers of two).  Each of the T
+// threads of a CTA holds V = W*L/T points in registers.  A length-L DFT runs
+// as Stockham autosort stages of radix 16 (then one radix 2/4/8 stage for the
+// remainder).  Stage with radix R after Ns points have been combined:
+//   butterfly (c, j), j < L/R, reads  a_r = line_c[j + r*L/R],
+//   multiplies a_r by w_{Ns*R}^{(j mod Ns)*r}, takes the R-point DFT, and
+//   writes  line_c[(j/Ns)*Ns*R + (j mod Ns) + r*Ns] = A_r.
+// The first stage reads global memory and the last writes it, both in the
+// coalesced "j + r*L/R" order; stages in between exchange through shared
+// memory.  This is the Cooley-Tukey FFT (Sec. I of the paper) in the
+// self-sorting Stockham arrangement, so the output is in natural order.
+//
+// w_M^m = exp(sigma * 2 pi i m / M); tables hold the forward value
+// (cos, -sin), evaluated in double on the host and rounded once to float.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define FDEV __device__ __forceinline__
+#define HDEV __host__ __device__ __forceinline__
+
+namespace fftseg {
+
+HDEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+HDEV float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// a * w for the forward table entry w; the inverse uses conj(w).
+template <int S>
+HDEV float2 twmul(float2 a, float2 w)
+{
+    if (S < 0) return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+    return make_float2(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y);
+}
+
+// a * (sigma i)
+template <int S>
+HDEV float2 mul_si(float2 a)
+{
+    return S < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+constexpr float kC8 = 0.70710678118654752440f;   // cos(pi/4)
+constexpr float kC16a = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kC16b = 0.38268343236508977173f;  // sin(pi/8)
+
+// a * w_16^M, w_16 = exp(sigma 2 pi i / 16), for the exponents a radix-16 butterfly needs
+template <int M, int S>
+HDEV float2 rot16(float2 a)
+{
+    constexpr float s = (float)S;
+    if (M == 0) return a;
+    if (M == 4) return mul_si<S>(a);
+    if (M == 2) return make_float2(kC8 * (a.x - s * a.y), kC8 * (a.y + s * a.x));
+    if (M == 6) return make_float2(kC8 * (-a.x - s * a.y), kC8 * (-a.y + s * a.x));
+    if (M == 1) return make_float2(a.x * kC16a - s * a.y * kC16b, a.y * kC16a + s * a.x * kC16b);
+    if (M == 3) return make_float2(a.x * kC16b - s * a.y * kC16a, a.y * kC16b + s * a.x * kC16a);
+    if (M == 9) return make_float2(-a.x * kC16a + s * a.y * kC16b, -a.y * kC16a - s * a.x * kC16b);
+    return a;  // not reached for the exponents used below
+}
+
+template <int S>
+HDEV void dft2(float2 &a, float2 &b)
+{
+    const float2 t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// X_k = sum_j v_j w_4^{jk}, in place, natural order.
+template <int S>
+HDEV void dft4(float2 &v0, float2 &v1, float2 &v2, float2 &v3)
+{
+    const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2);
+    const float2 a2 = cadd(v1, v3), a3 = mul_si<S>(csub(v1, v3));
+    v0 = cadd(a0, a2);
+    v2 = csub(a0, a2);
+    v1 = cadd(a1, a3);
+    v3 = csub(a1, a3);
+}
+
+// 8 = 2 x 4: X_k = E_k + w_8^k O_k, X_{k+4} = E_k - w_8^k O_k.
+template <int S>
+HDEV void dft8(float2 *v)
+{
+    float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<S>(e0, e1, e2, e3);
+    dft4<S>(o0, o1, o2, o3);
+    o1 = rot16<2, S>(o1);
+    o2 = rot16<4, S>(o2);
+    o3 = rot16<6, S>(o3);
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+// 16 = 4 x 4 with j = 4 j1 + j2 and k = k1 + 4 k2:
+//   Y[j2][k1] = w_16^{j2 k1} sum_{j1} v[4 j1 + j2] w_4^{j1 k1};
+//   X[k1 + 4 k2] = sum_{j2} Y[j2][k1] w_4^{j2 k2}.
+template <int S>
+HDEV void dft16(float2 *v)
+{
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) dft4<S>(v[j2], v[4 + j2], v[8 + j2], v[12 + j2]);
+    // v[j2 + 4 k1] = Y[j2][k1] before the twiddle
+    v[5] = rot16<1, S>(v[5]);
+    v[6] = rot16<2, S>(v[6]);
+    v[7] = rot16<3, S>(v[7]);
+    v[9] = rot16<2, S>(v[9]);
+    v[10] = rot16<4, S>(v[10]);
+    v[11] = rot16<6, S>(v[11]);
+    v[13] = rot16<3, S>(v[13]);
+    v[14] = rot16<6, S>(v[14]);
+    v[15] = rot16<9, S>(v[15]);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<S>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+    // v[4 k1 + k2] = X[k1 + 4 k2]; restore natural order
+    float2 t[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) t[k] = v[4 * (k & 3) + (k >> 2)];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = t[k];
+}
+
+template <int R, int S>
+HDEV void dft(float2 *v)
+{
+    if constexpr (R == 2) dft2<S>(v[0], v[1]);
+    else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
+    else if constexpr (R == 8) dft8<S>(v);
+    else if constexpr (R == 16) dft16<S>(v);
+}
+
+// Radix schedule of a length-2^LOG_L line: radix 16 while possible, then one
+// 2/4/8 stage.
+template <int LOG_L, int STAGE>
+struct StageInfo {
+    static constexpr int NFULL = LOG_L / 4;
+    static constexpr int REM = LOG_L % 4;
+    static constexpr int NSTAGES = NFULL + (REM ? 1 : 0);
+    static constexpr int LOG_R = (STAGE < NFULL) ? 4 : REM;
+    static constexpr int R = 1 << LOG_R;
+    static constexpr int LOG_NS = 4 * STAGE;
+    static constexpr int NS = 1 << LOG_NS;
+    static constexpr bool FIRST = STAGE == 0;
+    static constexpr bool LAST = STAGE == NSTAGES - 1;
+};
+
+// Shared-memory slot of (line c, index i).  CFAST: lines interleaved
+// (q = i*W + c); else line-major (q = c*L + i).  One pad slot every 2^PS
+// slots keeps the strided accesses of the first stage conflict-free.
+template <int LOG_L, int LOG_W, bool CFAST, int PS>
+FDEV int smem_slot(int c, int i)
+{
+    const int q = CFAST ? ((i << LOG_W) + c) : ((c << LOG_L) + i);
+    return q + (q >> PS);
+}
+
+template <int LOG_L, int LOG_W, int PS>
+constexpr int smem_slots()
+{
+    return (1 << (LOG_L + LOG_W)) + ((1 << (LOG_L + LOG_W)) >> PS) + 1;
+}
+
+// Butterfly g of a stage with radix 2^LOG_R -> (line c, butterfly index j).
+template <int LOG_L, int LOG_W, bool CFAST, int LOG_R>
+FDEV void butterfly_coords(int g, int &c, int &j)
+{
+    if (CFAST) {
+        c = g & ((1 << LOG_W) - 1);
+        j = g >> LOG_W;
+    } else {
+        c = g >> (LOG_L - LOG_R);
+        j = g & ((1 << (LOG_L - LOG_R)) - 1);
+    }
+}
+
+// Twiddle + DFT of one butterfly held in x[0..R).  twL: w_L^m, m < L.
+template <int LOG_L, int STAGE, int S>
+FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ twL)
+{
+    using I = StageInfo<LOG_L, STAGE>;
+    if constexpr (!I::FIRST) {
+        // w_{Ns R}^{(j mod Ns) r} = w_L^{(j mod Ns) r L/(Ns R)}
+        const int m = (j & (I::NS - 1)) << (LOG_L - I::LOG_NS - I::LOG_R);
+#pragma unroll
+        for (int r = 1; r < I::R; ++r) x[r] = twmul<S>(x[r], __ldg(twL + m * r));
+    }
+    dft<I::R, S>(x);
+}
+
+// Output index of element r of butterfly j.
+template <int LOG_L, int STAGE>
+FDEV int stockham_out_index(int j, int r)
+{
+    using I = StageInfo<LOG_L, STAGE>;
+    return ((j >> I::LOG_NS) << (I::LOG_NS + I::LOG_R)) + (j & (I::NS - 1)) + (r << I::LOG_NS);
+}
+
+}  // namespace fftseg

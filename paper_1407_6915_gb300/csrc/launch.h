@@ -1,0 +1,28 @@
+// Host-side launchers of the FP32 kernels (one translation unit per family).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace fftseg {
+
+// Single-pass segment-major tiles for n = 2^log_n <= 4096.  Launches
+// ceil(nseg / W) CTAs.  Returns the launch error.
+cudaError_t launch_block(int log_n, int sign, const LinesArgs &a, int64_t nseg, cudaStream_t st);
+// Segments per CTA of the block kernel.
+int block_segments_per_cta(int log_n);
+
+// One pass of the two-pass path over lines of length 2^log_l (16..4096),
+// interleaved tiles of 2^lines_log_w(log_l) lines; `units` CTAs.
+cudaError_t launch_pass(int log_l, int sign, const LinesArgs &a, int64_t units, cudaStream_t st);
+int pass_log_w(int log_l);
+
+// Single-pass cluster kernel for n = 2^log_n, 2^13..2^17; log_c selects the
+// cluster size where two are built (0 = default).
+cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, int64_t nseg,
+                           cudaStream_t st);
+// Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
+bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
+
+}  // namespace fftseg

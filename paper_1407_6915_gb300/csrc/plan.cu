@@ -1,0 +1,353 @@
+// Plans, twiddle tables, dispatch and the plain C-ABI entry points.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <vector>
+
+#include "launch.h"
+#include "plan.h"
+
+namespace fftseg {
+
+namespace {
+thread_local char g_msg[512] = "";
+std::atomic<int64_t> g_launches{0};
+
+constexpr int64_t kWorkTargetBytes = 32ll << 20;  // two-pass chunk: stays resident in L2
+constexpr int kTwoLevelAbove = 20;                 // n > 2^20: four-step table split in two
+constexpr int kTwLogK = 6;
+
+bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
+int ilog2(int64_t n)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+}  // namespace
+
+int set_error(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char *what)
+{
+    return set_error(e == cudaErrorMemoryAllocation ? FFTSEG_E_NOMEM : FFTSEG_E_CUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
+void count_launches(int64_t k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+void host_roots(float2 *t, int64_t count, int64_t M, int64_t stride_exp)
+{
+    // t[m] = exp(-2 pi i (m * stride_exp mod M) / M), the exponent reduced exactly in integers
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t m = 0; m < count; ++m) {
+        const int64_t e = (int64_t)(((unsigned __int128)m * (unsigned __int128)stride_exp) % (unsigned __int128)M);
+        const double a = two_pi * ((double)e / (double)M);
+        t[m] = make_float2((float)cos(a), (float)-sin(a));
+    }
+}
+
+namespace {
+
+int upload(float2 **dst, const std::vector<float2> &h)
+{
+    cudaError_t e = cudaMalloc((void **)dst, h.size() * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(twiddles)");
+    e = cudaMemcpy(*dst, h.data(), h.size() * sizeof(float2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "cudaMemcpy(twiddles)");
+    return FFTSEG_OK;
+}
+
+int roots_table(float2 **dst, int64_t M)
+{
+    std::vector<float2> h((size_t)M);
+    host_roots(h.data(), M, M, 1);
+    return upload(dst, h);
+}
+
+// Four-step table rows k1 < rows of w_n^{(k1 * row_mult) * j2}, [rows][n2]
+int fourstep_table(float2 **dst, int64_t n, int64_t rows, int64_t row_mult, int64_t n2)
+{
+    std::vector<float2> h((size_t)(rows * n2));
+    for (int64_t k1 = 0; k1 < rows; ++k1) host_roots(h.data() + k1 * n2, n2, n, k1 * row_mult);
+    return upload(dst, h);
+}
+
+void free_plan(fftseg_plan p)
+{
+    if (!p) return;
+    cudaFree(p->twA);
+    cudaFree(p->twB);
+    cudaFree(p->tw4a);
+    cudaFree(p->tw4b);
+    cudaFree(p->work);
+    if (p->tc) tc_plan_destroy(p);
+    delete p;
+}
+
+int build_fp32(fftseg_plan p)
+{
+    const int ln = p->log_n;
+    const bool force2 = (p->flags & FFTSEG_FLAG_FORCE_TWOPASS) && ln >= 8;
+    int rc;
+    if (ln <= 12 && !force2) {
+        p->path = PATH_BLOCK;
+        p->log_n1 = ln;
+        p->log_n2 = 0;
+        return roots_table(&p->twA, p->n);
+    }
+    int l1, l2, lc;
+    const int want_c = (int)((p->flags >> 8) & 0xFu);
+    if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: no cluster of 2^%d CTAs is built for n=2^%d",
+                         want_c, ln);
+    if (!force2 && cluster_shape(ln, want_c, &l1, &l2, &lc)) {
+        p->path = PATH_CLUSTER;
+        p->log_n1 = l1;
+        p->log_n2 = l2;
+        p->log_c = lc;
+        if ((rc = roots_table(&p->twA, int64_t(1) << l1))) return rc;
+        if ((rc = roots_table(&p->twB, int64_t(1) << l2))) return rc;
+        return fourstep_table(&p->tw4a, p->n, int64_t(1) << l1, 1, int64_t(1) << l2);
+    }
+    p->path = PATH_TWOPASS;
+    p->log_n1 = (ln + 1) / 2;  // column length (pass A)
+    p->log_n2 = ln / 2;        // row length (pass B)
+    const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
+    if ((rc = roots_table(&p->twA, n1))) return rc;
+    if ((rc = roots_table(&p->twB, n2))) return rc;
+    if (ln > kTwoLevelAbove) {
+        p->tw_log_k = kTwLogK;
+        const int64_t K = int64_t(1) << kTwLogK;
+        if ((rc = fourstep_table(&p->tw4a, p->n, K, 1, n2))) return rc;
+        if ((rc = fourstep_table(&p->tw4b, p->n, n1 / K, K, n2))) return rc;
+    } else {
+        p->tw_log_k = p->log_n1;
+        if ((rc = fourstep_table(&p->tw4a, p->n, n1, 1, n2))) return rc;
+    }
+    int64_t segs = kWorkTargetBytes / (p->n * 8);
+    if (segs < 1) segs = 1;
+    if (segs > p->batch) segs = p->batch;
+    p->work_segs = segs;
+    cudaError_t e = cudaMalloc((void **)&p->work, (size_t)(segs * p->n) * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(workspace)");
+    return FFTSEG_OK;
+}
+
+int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
+{
+    if (nseg <= 0) return 0;
+    switch (p->path) {
+        case PATH_BLOCK:
+        case PATH_CLUSTER: return 1;
+        case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
+        default: return tc_launches_per_exec(p);
+    }
+}
+
+}  // namespace
+
+int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
+{
+    if (nseg == 0) return FFTSEG_OK;
+    const float2 *in = static_cast<const float2 *>(d_in);
+    const int sign = p->direction;
+    const int power = p->out_kind == FFTSEG_OUT_POWER;
+    const int64_t n = p->n;
+    cudaError_t e = cudaSuccess;
+    switch (p->path) {
+        case PATH_BLOCK: {
+            LinesArgs a{};
+            const int64_t W = block_segments_per_cta(p->log_n);
+            a.in = in;
+            a.out = d_out;
+            a.tiles_per_seg = 1;
+            a.nseg = nseg;
+            a.in_seg = a.out_seg = W * n;
+            a.in_cs = a.out_cs = n;
+            a.in_is = a.out_is = 1;
+            a.twL = p->twA;
+            a.out_power = power;
+            a.scale = p->scale;
+            e = launch_block(p->log_n, sign, a, nseg, st);
+            if (e != cudaSuccess) return cuda_error(e, "block kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
+        case PATH_CLUSTER: {
+            ClusterArgs a{};
+            a.in = in;
+            a.out = d_out;
+            a.twA = p->twA;
+            a.twB = p->twB;
+            a.tw4 = p->tw4a;
+            a.out_power = power;
+            a.scale = p->scale;
+            e = launch_cluster(p->log_n, p->log_c, sign, a, nseg, st);
+            if (e != cudaSuccess) return cuda_error(e, "cluster kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
+        case PATH_TWOPASS: {
+            const int l1 = p->log_n1, l2 = p->log_n2;
+            const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+            const int64_t WA = int64_t(1) << pass_log_w(l1), WB = int64_t(1) << pass_log_w(l2);
+            for (int64_t s0 = 0; s0 < nseg; s0 += p->work_segs) {
+                const int64_t cnt = nseg - s0 < p->work_segs ? nseg - s0 : p->work_segs;
+                LinesArgs A{};  // columns: x[j1*n2 + j2] -> Y[k1*n2 + j2] * w_n^{k1 j2}
+                A.in = in + s0 * n;
+                A.out = p->work;
+                A.tiles_per_seg = n2 / WA;
+                A.nseg = cnt;
+                A.in_seg = A.out_seg = n;
+                A.in_tile = A.out_tile = WA;
+                A.in_cs = A.out_cs = 1;
+                A.in_is = A.out_is = n2;
+                A.twL = p->twA;
+                A.tw4a = p->tw4a;
+                A.tw4b = p->tw4b;
+                A.tw_ncols = n2;
+                A.tw_log_k = p->tw_log_k;
+                A.scale = 1.f;
+                e = launch_pass(l1, sign, A, cnt * (n2 / WA), st);
+                if (e != cudaSuccess) return cuda_error(e, "column pass launch");
+                LinesArgs B{};  // rows: Y[k1*n2 + j2] -> X[k1 + n1*k2]
+                B.in = p->work;
+                B.out = power ? (void *)(static_cast<float *>(d_out) + s0 * n)
+                              : (void *)(static_cast<float2 *>(d_out) + s0 * n);
+                B.tiles_per_seg = n1 / WB;
+                B.nseg = cnt;
+                B.in_seg = B.out_seg = n;
+                B.in_tile = WB * n2;
+                B.out_tile = WB;
+                B.in_cs = n2;
+                B.in_is = 1;
+                B.out_cs = 1;
+                B.out_is = n1;
+                B.twL = p->twB;
+                B.in_staged = 1;
+                B.out_power = power;
+                B.scale = p->scale;
+                e = launch_pass(l2, sign, B, cnt * (n1 / WB), st);
+                if (e != cudaSuccess) return cuda_error(e, "row pass launch");
+                count_launches(2);
+            }
+            return FFTSEG_OK;
+        }
+        case PATH_TC: return tc_exec(p, d_in, d_out, nseg, st);
+        default: return set_error(FFTSEG_E_INVALID, "corrupt plan");
+    }
+}
+
+}  // namespace fftseg
+
+using namespace fftseg;
+
+extern "C" {
+
+int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm,
+                       int precision, int out_kind, unsigned flags)
+{
+    if (!out) return set_error(FFTSEG_E_INVALID, "plan_create: out is NULL");
+    *out = nullptr;
+    if (!is_pow2(n) || n < 2 || n > (int64_t(1) << FFTSEG_MAX_LOG2N))
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: n=%lld is not a power of two in [2, 2^24]",
+                         (long long)n);
+    if (batch < 1) return set_error(FFTSEG_E_INVALID, "plan_create: batch must be >= 1");
+    if (direction != FFTSEG_FORWARD && direction != FFTSEG_INVERSE)
+        return set_error(FFTSEG_E_INVALID, "plan_create: direction must be -1 or +1");
+    if (norm < FFTSEG_NORM_NONE || norm > FFTSEG_NORM_ORTHO)
+        return set_error(FFTSEG_E_INVALID, "plan_create: bad norm %d", norm);
+    if (out_kind != FFTSEG_OUT_COMPLEX && out_kind != FFTSEG_OUT_POWER)
+        return set_error(FFTSEG_E_INVALID, "plan_create: bad out_kind %d", out_kind);
+    if (precision < FFTSEG_PREC_FP32 || precision > FFTSEG_PREC_TC_BF16)
+        return set_error(FFTSEG_E_INVALID, "plan_create: bad precision %d", precision);
+    if (batch > (int64_t(1) << 40) / n)
+        return set_error(FFTSEG_E_INVALID, "plan_create: batch*n too large");
+
+    fftseg_plan p = new (std::nothrow) fftseg_plan_s();
+    if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    p->n = n;
+    p->batch = batch;
+    p->log_n = ilog2(n);
+    p->direction = direction;
+    p->norm = norm;
+    p->precision = precision;
+    p->out_kind = out_kind;
+    p->flags = flags;
+    if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
+    else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
+    int rc = precision == FFTSEG_PREC_FP32 ? build_fp32(p) : tc_plan_create(p);
+    if (rc != FFTSEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FFTSEG_OK;
+}
+
+int fftseg_plan_destroy(fftseg_plan p)
+{
+    if (!p) return set_error(FFTSEG_E_INVALID, "plan_destroy: NULL plan");
+    free_plan(p);
+    return FFTSEG_OK;
+}
+
+int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, fftseg_stream_t stream)
+{
+    if (!p) return set_error(FFTSEG_E_INVALID, "exec: NULL plan");
+    if (nseg < 0 || nseg > p->batch)
+        return set_error(FFTSEG_E_INVALID, "exec: nseg=%lld outside [0, batch=%lld]", (long long)nseg,
+                         (long long)p->batch);
+    if (nseg == 0) return FFTSEG_OK;
+    if (!d_in || !d_out) return set_error(FFTSEG_E_INVALID, "exec: NULL buffer");
+    if (((uintptr_t)d_in & 15) || ((uintptr_t)d_out & 15))
+        return set_error(FFTSEG_E_INVALID, "exec: buffers must be 16-byte aligned");
+    if (d_in == d_out && p->out_kind == FFTSEG_OUT_POWER)
+        return set_error(FFTSEG_E_INVALID, "exec: the power output cannot be written in place");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
+    if (dev != p->device)
+        return set_error(FFTSEG_E_INVALID, "exec: plan belongs to device %d, current device is %d",
+                         p->device, dev);
+    return exec_plan(p, d_in, d_out, nseg, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int fftseg_exec(fftseg_plan p, const void *d_in, void *d_out, fftseg_stream_t stream)
+{
+    if (!p) return set_error(FFTSEG_E_INVALID, "exec: NULL plan");
+    return fftseg_exec_n(p, d_in, d_out, p->batch, stream);
+}
+
+int fftseg_plan_info(fftseg_plan p, int64_t info[6])
+{
+    if (!p || !info) return set_error(FFTSEG_E_INVALID, "plan_info: NULL argument");
+    info[0] = p->path;
+    info[1] = int64_t(1) << p->log_n1;
+    info[2] = p->path == PATH_BLOCK ? 1 : int64_t(1) << p->log_n2;
+    info[3] = p->work ? p->work_segs * p->n * 8 : 0;
+    info[4] = p->work_segs;
+    info[5] = launches_per_exec(p, p->batch);
+    return FFTSEG_OK;
+}
+
+const char *fftseg_last_error(void) { return g_msg; }
+
+int64_t fftseg_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

@@ -1,0 +1,62 @@
+// Plan object and host helpers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <string>
+
+#include "fftseg.h"
+
+namespace fftseg {
+
+enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_TC = 3 };
+
+struct TcPlan;  // tensor-core radix-16 state (tc.cu)
+
+}  // namespace fftseg
+
+struct fftseg_plan_s {
+    int device = 0;
+    int64_t n = 0, batch = 0;
+    int log_n = 0;
+    int direction = FFTSEG_FORWARD, norm = FFTSEG_NORM_NONE;
+    int precision = FFTSEG_PREC_FP32, out_kind = FFTSEG_OUT_COMPLEX;
+    unsigned flags = 0;
+    int path = 0;
+    int log_n1 = 0, log_n2 = 0, log_c = 0;
+    float scale = 1.f;
+    // twiddle tables (device, forward values w = exp(-2 pi i m / M))
+    float2 *twA = nullptr;   // w_{n1}^m (block: w_n^m)
+    float2 *twB = nullptr;   // w_{n2}^m
+    float2 *tw4a = nullptr;  // four-step twiddles, rows k1 mod 2^tw_log_k
+    float2 *tw4b = nullptr;  // rows k1 >> tw_log_k (null when one table is exact)
+    int tw_log_k = 0;
+    // two-pass workspace
+    float2 *work = nullptr;
+    int64_t work_segs = 0;
+    // fftseg_stream phase split of the last call (ms)
+    double phases[6] = {0, 0, 0, 0, 0, 0};
+    fftseg::TcPlan *tc = nullptr;
+};
+
+namespace fftseg {
+
+// error reporting (thread-local message)
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+void count_launches(int64_t k);
+
+// Run the plan on nseg segments (arguments already validated).
+int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);
+
+// Forward-direction roots of unity w_M^m for m < M, evaluated in double.
+void host_roots(float2 *t, int64_t count, int64_t M, int64_t stride_exp);
+
+// tensor-core path (tc.cu)
+int tc_plan_create(fftseg_plan p);
+void tc_plan_destroy(fftseg_plan p);
+int tc_exec(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);
+int64_t tc_launches_per_exec(fftseg_plan p);
+
+}  // namespace fftseg

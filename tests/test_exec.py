@@ -1,0 +1,175 @@
+"""GPU parity: fftseg_exec against the FP64 oracle on the same seeded inputs.
+
+Tolerance per result: relative L2 <= 2e-6*log2(n) (FP32 path).  Batches are
+ragged (segment counts that do not fill the last CTA / workspace chunk) and
+span many tiles.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from tests._util import rel_l2, tol_fp32, tol_power
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1407_6915_gb300 as fs  # noqa: E402
+
+FWD, INV = fs.FORWARD, fs.INVERSE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_6915_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def nseg_for(n, target=1 << 20):
+    # several tiles plus a ragged remainder
+    return max(3, target // n) + 1
+
+
+def run(plan, x_np, nseg=None):
+    x = torch.from_numpy(x_np).cuda()
+    y = plan.exec(x, nseg=nseg)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("log_n", list(range(1, 18)))
+@pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
+def test_single_pass_matches_oracle(log_n, direction, norm):
+    n = 1 << log_n
+    B = nseg_for(n)
+    x = siggen.uniform(100 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, direction, norm)
+    got = run(plan, x)
+    ref = oracle.fft(x, direction, norm)
+    err = rel_l2(got, ref)
+    assert err <= tol_fp32(n), (n, plan.info(), err)
+
+
+@pytest.mark.parametrize("log_n", [8, 9, 12, 13, 16, 17])
+@pytest.mark.parametrize("direction", [FWD, INV])
+def test_two_pass_forced_matches_oracle(log_n, direction):
+    n = 1 << log_n
+    B = nseg_for(n)
+    x = siggen.tones(200 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, direction, fs.NORM_NONE, flags=fs.FLAG_FORCE_TWOPASS)
+    assert plan.info()["path"] == "two-pass"
+    got = run(plan, x)
+    ref = oracle.fft(x, direction)
+    assert rel_l2(got, ref) <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n,B", [(18, 9), (19, 5), (20, 5), (21, 2), (22, 1)])
+def test_two_pass_large_matches_oracle(log_n, B):
+    n = 1 << log_n
+    x = siggen.tones(300 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD)
+    info = plan.info()
+    assert info["path"] == "two-pass"
+    got = run(plan, x)
+    ref = oracle.fft(x, FWD)
+    assert rel_l2(got, ref) <= tol_fp32(n), info
+
+
+def test_two_pass_2p24_matches_oracle():
+    n = 1 << 24
+    x = siggen.uniform(324, n).reshape(1, n)
+    plan = fs.Plan(n, 1, INV, fs.NORM_BACKWARD)
+    got = run(plan, x)
+    ref = oracle.fft(x, INV, fs.NORM_BACKWARD)
+    assert rel_l2(got, ref) <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n", [24, 20, 16])
+def test_impulse_closed_form_at_large_n(log_n):
+    # x = delta[j - j0]  =>  X[k] = exp(-2 pi i j0 k / n), checked at every k
+    n = 1 << log_n
+    j0 = 12345 % n
+    x = torch.zeros(n, dtype=torch.complex64, device="cuda")
+    x[j0] = 1.0
+    plan = fs.Plan(n, 1, FWD)
+    got = plan.exec(x).cpu().numpy().astype(np.complex128)
+    k = np.arange(n, dtype=np.int64)
+    ref = np.exp(-2j * np.pi * ((j0 * k) % n) / n)
+    assert rel_l2(got, ref) <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n", [10, 16, 20])
+def test_power_output(log_n):
+    n = 1 << log_n
+    B = max(2, (1 << 21) // n) + 1
+    x = siggen.tones(400 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD, out_kind=fs.OUT_POWER)
+    got = run(plan, x)
+    assert got.dtype == np.float32
+    ref = oracle.power(x, FWD)
+    assert rel_l2(got, ref) <= tol_power(n)
+
+
+@pytest.mark.parametrize("log_n", [6, 10, 14, 16, 18])
+def test_ortho_and_in_place(log_n):
+    n = 1 << log_n
+    B = nseg_for(n, 1 << 19)
+    x = siggen.uniform(500 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD, fs.NORM_ORTHO)
+    xd = torch.from_numpy(x).cuda()
+    plan.exec_ptr(xd.data_ptr(), xd.data_ptr())  # in place
+    got = xd.cpu().numpy()
+    assert rel_l2(got, oracle.fft(x, FWD, fs.NORM_ORTHO)) <= tol_fp32(n)
+    out_of_place = run(plan, x)
+    np.testing.assert_array_equal(out_of_place, got)  # same kernels, same bits
+
+
+@pytest.mark.parametrize("log_n", [10, 16, 20])
+def test_partial_batch_and_empty(log_n):
+    n = 1 << log_n
+    B = 7
+    x = siggen.uniform(600 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.full((B, n), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
+    plan.exec(xd, out=out, nseg=3)
+    got = out.cpu().numpy()
+    assert rel_l2(got[:3], oracle.fft(x[:3], FWD)) <= tol_fp32(n)
+    assert np.all(got[3:] == np.complex64(complex(7.0, -7.0)))  # nothing past nseg is written
+    plan.exec(xd, out=out, nseg=0)
+    with pytest.raises(fs.FFTSegError):
+        plan.exec(xd, out=out, nseg=B + 1)
+
+
+def test_round_trip_and_determinism():
+    n, B = 1 << 16, 33
+    x = siggen.tones(700, B * n).reshape(B, n)
+    xd = torch.from_numpy(x).cuda()
+    fwd = fs.Plan(n, B, FWD)
+    inv = fs.Plan(n, B, INV, fs.NORM_BACKWARD)
+    X1 = fwd.exec(xd)
+    X2 = fwd.exec(xd)
+    assert torch.equal(X1, X2)
+    back = inv.exec(X1).cpu().numpy()
+    assert rel_l2(back, x) <= 2 * tol_fp32(n)
+
+
+def test_misaligned_pointer_rejected():
+    n = 1024
+    plan = fs.Plan(n, 1, FWD)
+    x = torch.zeros(n + 2, dtype=torch.complex64, device="cuda")
+    with pytest.raises(fs.FFTSegError) as ei:
+        plan.exec_ptr(x.data_ptr() + 8, x.data_ptr())
+    assert ei.value.status == fs.E_INVALID
+
+
+def test_launch_counter_counts_kernels():
+    n, B = 1 << 20, 9
+    plan = fs.Plan(n, B, FWD)
+    x = torch.zeros(B, n, dtype=torch.complex64, device="cuda")
+    before = fs.launch_count()
+    plan.exec(x)
+    assert fs.launch_count() - before == plan.info()["launches_per_exec"]
