@@ -137,6 +137,11 @@ int fftseg_plan_destroy(fftseg_plan p);
  * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
 int fftseg_plan_info(fftseg_plan p, int64_t info[6]);
 
+/* Synchronise with the device and report whether any kernel of this plan
+ * gave up a bounded wait since the last check (FFTSEG_E_TIMEOUT; the outputs
+ * of that call are then not valid) -- FFTSEG_OK otherwise.  Clears the flag. */
+int fftseg_plan_check(fftseg_plan p);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char *fftseg_last_error(void);
 

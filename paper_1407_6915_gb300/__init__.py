@@ -71,6 +71,7 @@ _SIGS = {
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "fftseg_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fftseg_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
+    "fftseg_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
     "fftseg_last_error": (ctypes.c_char_p, []),
     "fftseg_launch_count": (ctypes.c_int64, []),
     "fftsrv_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(SrvConfig)]),
@@ -196,6 +197,10 @@ class Plan:
         if rc not in (OK, E_IO, E_PARTIAL):
             check(rc, "fftseg_stream")
         return rc, committed.value
+
+    def check(self) -> None:
+        """Synchronise and raise if a kernel of this plan gave up a bounded wait."""
+        check(lib().fftseg_plan_check(self._h), "fftseg_plan_check")
 
     def stream_phases(self) -> dict:
         a = (ctypes.c_double * 6)()

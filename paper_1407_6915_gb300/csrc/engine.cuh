@@ -15,6 +15,7 @@
 // w_M^m = exp(sigma * 2 pi i m / M); tables hold the forward value
 // (cos, -sin), evaluated in double on the host and rounded once to float.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -182,16 +183,33 @@ FDEV void butterfly_coords(int g, int &c, int &j)
     }
 }
 
-// Twiddle + DFT of one butterfly held in x[0..R).  twL: w_L^m, m < L.
+// Stage twiddle tables.  Stage s > 0 (radix R, Ns = 16^s) multiplies element
+// r of butterfly j by w_{Ns R}^{m r}, m = j mod Ns.  Its table holds these
+// values r-major, [r-1][m], so that lanes with consecutive m read consecutive
+// entries (or one broadcast entry); tables of stages 1, 2, ... follow each
+// other.  stage_table_offset gives where stage s starts.
+template <int LOG_L>
+__host__ __device__ constexpr int stage_table_offset(int stage)
+{
+    int off = 0;
+    for (int s = 1; s < stage; ++s) {
+        const int lr = s < LOG_L / 4 ? 4 : LOG_L % 4;
+        off += ((1 << lr) - 1) << (4 * s);
+    }
+    return off;
+}
+
+// Twiddle + DFT of one butterfly held in x[0..R).  tw: the stage tables of
+// a length-L line (see StageTable).
 template <int LOG_L, int STAGE, int S>
-FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ twL)
+FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ tw)
 {
     using I = StageInfo<LOG_L, STAGE>;
     if constexpr (!I::FIRST) {
-        // w_{Ns R}^{(j mod Ns) r} = w_L^{(j mod Ns) r L/(Ns R)}
-        const int m = (j & (I::NS - 1)) << (LOG_L - I::LOG_NS - I::LOG_R);
+        constexpr int OFF = stage_table_offset<LOG_L>(STAGE);
+        const float2 *t = tw + OFF + (j & (I::NS - 1));
 #pragma unroll
-        for (int r = 1; r < I::R; ++r) x[r] = twmul<S>(x[r], __ldg(twL + m * r));
+        for (int r = 1; r < I::R; ++r) x[r] = twmul<S>(x[r], __ldg(t + (r - 1) * I::NS));
     }
     dft<I::R, S>(x);
 }
@@ -202,6 +220,93 @@ FDEV int stockham_out_index(int j, int r)
 {
     using I = StageInfo<LOG_L, STAGE>;
     return ((j >> I::LOG_NS) << (I::LOG_NS + I::LOG_R)) + (j & (I::NS - 1)) + (r << I::LOG_NS);
+}
+
+}  // namespace fftseg
+
+// ------------------------------------------------------------------ TMA bulk
+// 1-D bulk copies global -> shared (cp.async.bulk), completed on an mbarrier
+// with transaction-byte accounting.  Every wait is bounded: after
+// kSpinLimit polls the waiter records a timeout in *err and carries on, so a
+// lost copy can never hang the GPU.
+namespace fftseg {
+
+constexpr uint32_t kSpinLimit = 1u << 24;
+
+FDEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+FDEV void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+FDEV void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// order this thread's earlier generic-proxy shared-memory accesses before
+// later async-proxy (TMA) accesses
+FDEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+FDEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst (shared, 16-byte aligned) <- src (global, 16-byte aligned), bytes % 16 == 0
+FDEV void tma_load_1d(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Tiled 3-D TMA load of one box of `tmap` at element coordinates (x, y, z)
+// into shared memory (16-byte aligned), completed on *bar.  x * 8 bytes must
+// be a multiple of 16 (8-byte elements: x even).
+FDEV void tma_load_3d(void *dst, const CUtensorMap *tmap, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// address of the same shared-memory variable in CTA `rank` of the cluster
+FDEV uint32_t mapa_u32(uint32_t smem_addr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr), "r"(rank));
+    return r;
+}
+
+FDEV void st_cluster_v2(uint32_t addr, float2 v)
+{
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+FDEV bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of *bar; false (and *err set) if it never completes.
+FDEV bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)
+{
+    for (uint32_t it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicOr(err, 1);
+    return false;
 }
 
 }  // namespace fftseg

@@ -6,31 +6,48 @@ namespace fftseg {
 namespace {
 
 template <int LOG_N1, int LOG_N2, int LOG_C, int S>
-cudaError_t cluster_t(const ClusterArgs &a, int64_t nseg, cudaStream_t st)
+cudaError_t cluster_t(const ClusterArgs &a, cudaStream_t st)
 {
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
     auto k = k_cluster<LOG_N1, LOG_N2, LOG_C, S>;
-    const size_t smem = (size_t)Sh::SLOTS * sizeof(float2);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = Sh::C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(Sh::T);
+    cfg.dynamicSmemBytes = Sh::SMEM;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = 0;
+    if (max_clusters == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         if (e != cudaSuccess) return e;
         if (Sh::C > 8) {
             e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
         }
-        configured = true;
+        int m = 0;
+        cfg.gridDim = dim3(Sh::C * 1024);
+        e = cudaOccupancyMaxActiveClusters(&m, k, &cfg);
+        if (e != cudaSuccess) return e;
+        if (m < 1) return cudaErrorLaunchOutOfResources;
+        max_clusters = m;
     }
-    if (nseg == 0) return cudaSuccess;
-    k<<<(unsigned)(nseg * Sh::C), Sh::T, smem, st>>>(a);
+    if (a.nseg == 0) return cudaSuccess;
+    const int64_t ncl = a.nseg < max_clusters ? a.nseg : max_clusters;
+    cfg.gridDim = dim3((unsigned)(ncl * Sh::C));
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 template <int LOG_N1, int LOG_N2, int LOG_C>
-cudaError_t cluster_s(int sign, const ClusterArgs &a, int64_t nseg, cudaStream_t st)
+cudaError_t cluster_s(int sign, const ClusterArgs &a, cudaStream_t st)
 {
-    return sign < 0 ? cluster_t<LOG_N1, LOG_N2, LOG_C, -1>(a, nseg, st)
-                    : cluster_t<LOG_N1, LOG_N2, LOG_C, 1>(a, nseg, st);
+    return sign < 0 ? cluster_t<LOG_N1, LOG_N2, LOG_C, -1>(a, st) : cluster_t<LOG_N1, LOG_N2, LOG_C, 1>(a, st);
 }
 
 }  // namespace
@@ -50,17 +67,16 @@ bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_
     }
 }
 
-cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, int64_t nseg,
-                           cudaStream_t st)
+cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, cudaStream_t st)
 {
     int l1, l2, lc;
     if (!cluster_shape(log_n, log_c, &l1, &l2, &lc)) return cudaErrorInvalidValue;
     switch (log_n) {
-        case 13: return cluster_s<6, 7, 1>(sign, a, nseg, st);
-        case 14: return cluster_s<7, 7, 2>(sign, a, nseg, st);
-        case 15: return cluster_s<7, 8, 3>(sign, a, nseg, st);
-        case 16: return lc == 4 ? cluster_s<8, 8, 4>(sign, a, nseg, st) : cluster_s<8, 8, 3>(sign, a, nseg, st);
-        case 17: return cluster_s<8, 9, 4>(sign, a, nseg, st);
+        case 13: return cluster_s<6, 7, 1>(sign, a, st);
+        case 14: return cluster_s<7, 7, 2>(sign, a, st);
+        case 15: return cluster_s<7, 8, 3>(sign, a, st);
+        case 16: return lc == 4 ? cluster_s<8, 8, 4>(sign, a, st) : cluster_s<8, 8, 3>(sign, a, st);
+        case 17: return cluster_s<8, 9, 4>(sign, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -6,31 +6,37 @@ namespace fftseg {
 
 namespace {
 
-template <int LOG_L>
-struct BlockShape {
-    // 16 points per thread, 256 threads, 4096 points per CTA; lines shorter
-    // than 16 points put L points in a thread and 256 lines in a CTA.
-    static constexpr int LOG_W = LOG_L >= 4 ? 12 - LOG_L : 8;
-    static constexpr int T = 256;
-    static constexpr int SLOTS = smem_slots<LOG_L, LOG_W, 4>();
-};
+int g_sm_count = 0;
+
+int sm_count()
+{
+    if (g_sm_count == 0) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sm_count = v > 0 ? v : 1;
+    }
+    return g_sm_count;
+}
 
 template <int LOG_L, int S>
-cudaError_t block_t(const LinesArgs &a, int64_t nseg, cudaStream_t st)
+cudaError_t block_t(const BlockArgs &a, cudaStream_t st)
 {
     using B = BlockShape<LOG_L>;
-    auto k = k_lines<LOG_L, B::LOG_W, false, S, B::T>;
-    const size_t smem = (size_t)B::SLOTS * sizeof(float2);
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto k = k_block<LOG_L, S>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
         if (e != cudaSuccess) return e;
-        configured = true;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B::T, B::SMEM);
+        if (e != cudaSuccess) return e;
+        per_sm = occ > 0 ? occ : 1;
     }
-    const int64_t per = 1 << B::LOG_W;
-    const int64_t grid = (nseg + per - 1) / per;
-    if (grid == 0) return cudaSuccess;
-    k<<<(unsigned)grid, B::T, smem, st>>>(a);
+    if (a.ntiles == 0) return cudaSuccess;
+    int64_t grid = (int64_t)per_sm * sm_count();
+    if (grid > a.ntiles) grid = a.ntiles;
+    k<<<(unsigned)grid, B::T, B::SMEM, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -66,15 +72,17 @@ int block_segments_per_cta(int log_n)
     return log_n >= 4 ? 1 << (12 - log_n) : 256;
 }
 
+int device_sm_count() { return sm_count(); }
+
 int pass_log_w(int log_l)
 {
     return (14 - log_l) < 4 ? (14 - log_l) : 4;
 }
 
 #define FFTSEG_BLOCK_CASE(LL) \
-    case LL: return sign < 0 ? block_t<LL, -1>(a, nseg, st) : block_t<LL, 1>(a, nseg, st);
+    case LL: return sign < 0 ? block_t<LL, -1>(a, st) : block_t<LL, 1>(a, st);
 
-cudaError_t launch_block(int log_n, int sign, const LinesArgs &a, int64_t nseg, cudaStream_t st)
+cudaError_t launch_block(int log_n, int sign, const BlockArgs &a, cudaStream_t st)
 {
     switch (log_n) {
         FFTSEG_BLOCK_CASE(1)

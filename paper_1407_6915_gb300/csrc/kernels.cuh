@@ -54,8 +54,10 @@ FDEV void scatter_last(const float2 *v, Put &&put)
 
 // Run stages STAGE..last on the values in v (this stage's inputs).  Between
 // stages the tile goes through shared memory `sm` (layout smem_slot<..., PS>).
-// After the last butterflies the outputs stay in v for the caller.
-template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE>
+// After the last butterflies the outputs stay in v for the caller.  IN_SM:
+// this stage's inputs were read from `sm` (so a barrier must separate those
+// reads from the writes below).
+template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true>
 FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
 {
     using I = StageInfo<LOG_L, STAGE>;
@@ -67,7 +69,7 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
         butterfly<LOG_L, STAGE, S>(v + b * I::R, j, twL);
     }
     if constexpr (!I::LAST) {
-        __syncthreads();  // every thread has read this stage's inputs from sm
+        if constexpr (IN_SM) __syncthreads();  // every thread has read this stage's inputs from sm
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             int c, j;
@@ -97,7 +99,7 @@ struct LinesArgs {
     int64_t in_tile, out_tile;  // element stride between tiles of one segment
     int64_t in_cs, in_is;       // input: stride between lines, between points of a line
     int64_t out_cs, out_is;     // output: same
-    const float2 *twL;          // w_L^m, m < L
+    const float2 *twL;          // stage twiddle tables of a length-L line
     const float2 *tw4a;         // four-step twiddle rows k1 mod 2^tw_log_k, [2^tw_log_k][tw_ncols], or null
     const float2 *tw4b;         // rows k1 >> tw_log_k, [n1 >> tw_log_k][tw_ncols], or null
     int64_t tw_ncols;
@@ -159,14 +161,103 @@ __global__ void __launch_bounds__(T) k_lines(const LinesArgs a)
     });
 }
 
+// --------------------------------------------------------------------- k_block
+
+// Single-pass segment-major tiles (n <= 4096).  Persistent: each CTA walks
+// tiles u, u + gridDim.x, ...; tile u (W whole segments, contiguous in memory)
+// arrives by one TMA bulk copy into a double buffer while the previous tile
+// is being transformed.
+struct BlockArgs {
+    const float2 *in;
+    void *out;
+    int64_t nseg;
+    int64_t ntiles;
+    const float2 *twL;  // stage twiddle tables of a length-n line
+    int *err;           // set to 1 if a copy never completed
+    int out_power;
+    float scale;
+};
+
+template <int LOG_L>
+struct BlockShape {
+    // 16 points per thread, 256 threads, 4096 points per tile; lines shorter
+    // than 16 points put L points in a thread and 256 lines in a tile.
+    static constexpr int LOG_W = LOG_L >= 4 ? 12 - LOG_L : 8;
+    static constexpr int T = 256;
+    static constexpr int E = 1 << (LOG_L + LOG_W);
+    static constexpr int PS = 4;
+    static constexpr int SLOTS = (smem_slots<LOG_L, LOG_W, PS>() + 1) & ~1;  // keeps the barriers 8-byte aligned
+    static constexpr size_t SMEM = (size_t)(SLOTS + 2 * E) * sizeof(float2) + 2 * sizeof(uint64_t);
+};
+
+template <int LOG_L, int S>
+__global__ void __launch_bounds__(256, 2) k_block(const BlockArgs a)
+{
+    using Sh = BlockShape<LOG_L>;
+    constexpr int L = 1 << LOG_L, W = 1 << Sh::LOG_W, E = Sh::E, T = Sh::T, V = E / T;
+    // TMA destinations first: the dynamic shared base is 1024-byte aligned and
+    // each prefetch buffer is a multiple of 1024 bytes
+    extern __shared__ __align__(1024) float2 sm[];
+    float2 *P = sm;
+    float2 *X = sm + 2 * E;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
+    const int tid = threadIdx.x;
+    if (smem_u32(P) & 127) {  // never expected; refuse rather than issue a misaligned copy
+        if (tid == 0) atomicOr(a.err, 2);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int64_t u, int b) {
+        if (tid == 0) {
+            int64_t segs = a.nseg - u * W;
+            if (segs > W) segs = W;
+            const uint32_t bytes = (uint32_t)(segs * L * (int64_t)sizeof(float2));
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b], bytes);
+            tma_load_1d(P + b * E, a.in + u * E, bytes, &bar[b]);
+        }
+    };
+
+    int64_t u = blockIdx.x;
+    if (u < a.ntiles) issue(u, 0);
+    const float scale = a.scale;
+    for (int k = 0; u < a.ntiles; u += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (u + gridDim.x < a.ntiles) issue(u + gridDim.x, b ^ 1);
+        mbar_wait(&bar[b], (k >> 1) & 1, a.err);
+        const float2 *Pb = P + b * E;
+        float2 v[V];
+        gather<LOG_L, Sh::LOG_W, false, T, 0>(v, [&](int c, int i) { return Pb[(c << LOG_L) + i]; });
+        run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false>(v, X, a.twL);
+        const int64_t line0 = u * W;
+        scatter_last<LOG_L, Sh::LOG_W, false, T>(v, [&](int c, int i, float2 x) {
+            if (line0 + c >= a.nseg) return;
+            if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
+            const int64_t o = (line0 + c) * L + i;
+            if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
+            else static_cast<float2 *>(a.out)[o] = x;
+        });
+        __syncthreads();  // P[b] fully read before it is refilled two tiles on
+    }
+}
+
 // ------------------------------------------------------------------- k_cluster
 
 struct ClusterArgs {
+    CUtensorMap tmap;  // the input as [nseg][N1][N2] 8-byte elements, box [1][N1][WA]
     const float2 *in;
     void *out;
-    const float2 *twA;  // w_{N1}^m
-    const float2 *twB;  // w_{N2}^m
+    int64_t nseg;
+    const float2 *twA;  // stage twiddle tables, length N1
+    const float2 *twB;  // stage twiddle tables, length N2
     const float2 *tw4;  // w_n^{k1 j2}, [N1][N2]
+    int *err;
     int out_power;
     float scale;
 };
@@ -182,49 +273,93 @@ struct ClusterShape {
     static constexpr int PSB = LOG_WB < 4 ? 4 : LOG_WB;
     static constexpr int SLOTS_A = smem_slots<LOG_N1, LOG_WA, PSA>();
     static constexpr int SLOTS_B = smem_slots<LOG_N2, LOG_WB, PSB>();
-    static constexpr int SLOTS = SLOTS_A > SLOTS_B ? SLOTS_A : SLOTS_B;
+    static constexpr int SLOTS = ((SLOTS_A > SLOTS_B ? SLOTS_A : SLOTS_B) + 1) & ~1;
+    static constexpr size_t SMEM = (size_t)(SLOTS + 2 * E) * sizeof(float2) + 2 * sizeof(uint64_t);
+    static constexpr int MINB = T <= 256 ? 2 : 1;  // CTAs per SM the register budget must allow
 };
 
+// One cluster of C CTAs per segment, persistent over segments
+// s = cluster, cluster + nclusters, ...  CTA r of the cluster receives the
+// column slab j2 in [r*WA, (r+1)*WA) of the next segment (N1 rows of WA
+// points) by one tiled TMA copy while it works on the current one.
 template <int LOG_N1, int LOG_N2, int LOG_C, int S>
-__global__ void __cluster_dims__(1 << LOG_C, 1, 1)
-    __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T) k_cluster(const ClusterArgs a)
+__global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, ClusterShape<LOG_N1, LOG_N2, LOG_C>::MINB)
+    k_cluster(const __grid_constant__ ClusterArgs a)
 {
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
-    constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2, T = Sh::T;
+    constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2, T = Sh::T, E = Sh::E;
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
-    extern __shared__ float2 sm[];
+    constexpr int64_t N = (int64_t)N1 * N2;
+    // tiled TMA writes need a 128-byte aligned destination: the prefetch
+    // buffers come first (base 1024-byte aligned, each a multiple of 1024 bytes)
+    extern __shared__ __align__(1024) float2 sm[];
+    float2 *P = sm;
+    float2 *X = sm + 2 * E;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
-    const int64_t seg = blockIdx.x >> LOG_C;
-    const float2 *__restrict__ in = a.in + seg * ((int64_t)N1 * N2);
-    float2 v[16];
+    const int tid = threadIdx.x;
+    if (smem_u32(P) & 127) {  // same layout in every CTA: the whole cluster leaves together
+        if (tid == 0) atomicOr(a.err, 2);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
 
-    // column pass: line c is column j2 = rank*WA + c, points at j1*N2 + j2
-    gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return in[i * N2 + rank * WA + c]; });
-    run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0>(v, sm, a.twA);
+    auto issue = [&](int64_t s, int b) {
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b], (uint32_t)(E * sizeof(float2)));
+            tma_load_3d(P + b * E, &a.tmap, rank * WA, 0, (int)s, &bar[b]);
+        }
+    };
 
-    cl.sync();  // every CTA of the cluster is done with its own buffer
-    scatter_last<LOG_N1, Sh::LOG_WA, true, T>(v, [&](int c, int k1, float2 x) {
-        const int j2 = rank * WA + c;
-        x = twmul<S>(x, __ldg(a.tw4 + k1 * N2 + j2));
-        float2 *dst = cl.map_shared_rank(sm, k1 >> Sh::LOG_WB);
-        dst[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(k1 & (WB - 1), j2)] = x;
-    });
-    cl.sync();  // every row this CTA owns has arrived
+    uint32_t xrank[Sh::C];  // X of every CTA of the cluster, as shared::cluster addresses
+#pragma unroll
+    for (int q = 0; q < Sh::C; ++q) xrank[q] = mapa_u32(smem_u32(X), q);
 
-    // row pass: line c is row k1 = rank*WB + c, points over j2
-    gather<LOG_N2, Sh::LOG_WB, true, T, 0>(
-        v, [&](int c, int i) { return sm[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(c, i)]; });
-    run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0>(v, sm, a.twB);
-
+    const int64_t cid = blockIdx.x >> LOG_C, ncl = gridDim.x >> LOG_C;
+    int64_t s = cid;
+    if (s < a.nseg) issue(s, 0);
     const float scale = a.scale;
-    const int64_t obase = seg * ((int64_t)N1 * N2) + rank * WB;
-    scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
-        if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
-        const int64_t o = obase + (int64_t)k2 * N1 + c;
-        if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
-        else static_cast<float2 *>(a.out)[o] = x;
-    });
+    for (int k = 0; s < a.nseg; s += ncl, ++k) {
+        const int b = k & 1;
+        if (s + ncl < a.nseg) issue(s + ncl, b ^ 1);
+        mbar_wait(&bar[b], (k >> 1) & 1, a.err);
+        const float2 *Pb = P + b * E;
+        float2 v[16];
+
+        // column pass: line c is column j2 = rank*WA + c, points j1 = i
+        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return Pb[i * WA + c]; });
+        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, false>(v, X, a.twA);
+
+        cl.sync();  // every CTA of the cluster is done with its own X
+        scatter_last<LOG_N1, Sh::LOG_WA, true, T>(v, [&](int c, int k1, float2 x) {
+            const int j2 = rank * WA + c;
+            x = twmul<S>(x, __ldg(a.tw4 + k1 * N2 + j2));
+            const uint32_t slot = smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(k1 & (WB - 1), j2);
+            st_cluster_v2(xrank[k1 >> Sh::LOG_WB] + slot * (uint32_t)sizeof(float2), x);
+        });
+        cl.sync();  // every row this CTA owns has arrived
+
+        // row pass: line c is row k1 = rank*WB + c, points j2 = i
+        gather<LOG_N2, Sh::LOG_WB, true, T, 0>(
+            v, [&](int c, int i) { return X[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(c, i)]; });
+        run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0>(v, X, a.twB);
+
+        const int64_t obase = s * N + rank * WB;
+        scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
+            if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
+            const int64_t o = obase + (int64_t)k2 * N1 + c;
+            if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
+            else static_cast<float2 *>(a.out)[o] = x;
+        });
+    }
+    cl.sync();  // no CTA leaves while a peer could still write into its X
 }
 
 }  // namespace fftseg

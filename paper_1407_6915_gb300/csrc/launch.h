@@ -7,9 +7,10 @@
 
 namespace fftseg {
 
-// Single-pass segment-major tiles for n = 2^log_n <= 4096.  Launches
-// ceil(nseg / W) CTAs.  Returns the launch error.
-cudaError_t launch_block(int log_n, int sign, const LinesArgs &a, int64_t nseg, cudaStream_t st);
+// Single-pass segment-major tiles for n = 2^log_n <= 4096 (persistent CTAs,
+// a.ntiles tiles of block_segments_per_cta segments).  Returns the launch error.
+cudaError_t launch_block(int log_n, int sign, const BlockArgs &a, cudaStream_t st);
+int device_sm_count();
 // Segments per CTA of the block kernel.
 int block_segments_per_cta(int log_n);
 
@@ -20,8 +21,7 @@ int pass_log_w(int log_l);
 
 // Single-pass cluster kernel for n = 2^log_n, 2^13..2^17; log_c selects the
 // cluster size where two are built (0 = default).
-cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, int64_t nseg,
-                           cudaStream_t st);
+cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, cudaStream_t st);
 // Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
 bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
 

@@ -67,10 +67,27 @@ int upload(float2 **dst, const std::vector<float2> &h)
     return FFTSEG_OK;
 }
 
-int roots_table(float2 **dst, int64_t M)
+// Stage twiddle tables of a length-L line, in the order the kernels read them:
+// for every stage s >= 1 (radix R_s, Ns = 16^s combined points before it),
+// entries [r-1][m] = w_{Ns R_s}^{m r}, r = 1..R_s-1, m = 0..Ns-1.  The radix
+// schedule is 16, 16, ..., then one 2/4/8 stage for the remainder.
+int stage_table(float2 **dst, int64_t L)
 {
-    std::vector<float2> h((size_t)M);
-    host_roots(h.data(), M, M, 1);
+    int log_l = ilog2(L);
+    std::vector<float2> h;
+    int64_t ns = 1;
+    for (int left = log_l; left > 0;) {
+        const int lr = left >= 4 ? 4 : left;
+        const int64_t R = int64_t(1) << lr;
+        if (ns > 1) {
+            const size_t base = h.size();
+            h.resize(base + (size_t)((R - 1) * ns));
+            for (int64_t r = 1; r < R; ++r) host_roots(h.data() + base + (r - 1) * ns, ns, ns * R, r);
+        }
+        ns *= R;
+        left -= lr;
+    }
+    if (h.empty()) h.push_back(make_float2(1.f, 0.f));
     return upload(dst, h);
 }
 
@@ -90,6 +107,7 @@ void free_plan(fftseg_plan p)
     cudaFree(p->tw4a);
     cudaFree(p->tw4b);
     cudaFree(p->work);
+    cudaFree(p->d_err);
     if (p->tc) tc_plan_destroy(p);
     delete p;
 }
@@ -103,7 +121,7 @@ int build_fp32(fftseg_plan p)
         p->path = PATH_BLOCK;
         p->log_n1 = ln;
         p->log_n2 = 0;
-        return roots_table(&p->twA, p->n);
+        return stage_table(&p->twA, p->n);
     }
     int l1, l2, lc;
     const int want_c = (int)((p->flags >> 8) & 0xFu);
@@ -115,16 +133,16 @@ int build_fp32(fftseg_plan p)
         p->log_n1 = l1;
         p->log_n2 = l2;
         p->log_c = lc;
-        if ((rc = roots_table(&p->twA, int64_t(1) << l1))) return rc;
-        if ((rc = roots_table(&p->twB, int64_t(1) << l2))) return rc;
+        if ((rc = stage_table(&p->twA, int64_t(1) << l1))) return rc;
+        if ((rc = stage_table(&p->twB, int64_t(1) << l2))) return rc;
         return fourstep_table(&p->tw4a, p->n, int64_t(1) << l1, 1, int64_t(1) << l2);
     }
     p->path = PATH_TWOPASS;
     p->log_n1 = (ln + 1) / 2;  // column length (pass A)
     p->log_n2 = ln / 2;        // row length (pass B)
     const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
-    if ((rc = roots_table(&p->twA, n1))) return rc;
-    if ((rc = roots_table(&p->twB, n2))) return rc;
+    if ((rc = stage_table(&p->twA, n1))) return rc;
+    if ((rc = stage_table(&p->twB, n2))) return rc;
     if (ln > kTwoLevelAbove) {
         p->tw_log_k = kTwLogK;
         const int64_t K = int64_t(1) << kTwLogK;
@@ -156,6 +174,20 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
 
 }  // namespace
 
+int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1)
+{
+    const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+    const cuuint64_t strides[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
+    const cuuint32_t box[3] = {box0, box1, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = cuTensorMapEncodeTiled(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides,
+                                        box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FFTSEG_OK;
+}
+
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
     if (nseg == 0) return FFTSEG_OK;
@@ -166,33 +198,37 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
     cudaError_t e = cudaSuccess;
     switch (p->path) {
         case PATH_BLOCK: {
-            LinesArgs a{};
+            BlockArgs a{};
             const int64_t W = block_segments_per_cta(p->log_n);
             a.in = in;
             a.out = d_out;
-            a.tiles_per_seg = 1;
             a.nseg = nseg;
-            a.in_seg = a.out_seg = W * n;
-            a.in_cs = a.out_cs = n;
-            a.in_is = a.out_is = 1;
+            a.ntiles = (nseg + W - 1) / W;
             a.twL = p->twA;
+            a.err = p->d_err;
             a.out_power = power;
             a.scale = p->scale;
-            e = launch_block(p->log_n, sign, a, nseg, st);
+            e = launch_block(p->log_n, sign, a, st);
             if (e != cudaSuccess) return cuda_error(e, "block kernel launch");
             count_launches(1);
             return FFTSEG_OK;
         }
         case PATH_CLUSTER: {
             ClusterArgs a{};
+            const int64_t N1 = int64_t(1) << p->log_n1, N2 = int64_t(1) << p->log_n2;
+            const uint32_t WA = (uint32_t)(N2 >> p->log_c);
+            int rc = encode_tmap_3d(&a.tmap, in, N2, N1, nseg, N2 * 8, n * 8, WA, (uint32_t)N1);
+            if (rc != FFTSEG_OK) return rc;
             a.in = in;
             a.out = d_out;
+            a.nseg = nseg;
+            a.err = p->d_err;
             a.twA = p->twA;
             a.twB = p->twB;
             a.tw4 = p->tw4a;
             a.out_power = power;
             a.scale = p->scale;
-            e = launch_cluster(p->log_n, p->log_c, sign, a, nseg, st);
+            e = launch_cluster(p->log_n, p->log_c, sign, a, st);
             if (e != cudaSuccess) return cuda_error(e, "cluster kernel launch");
             count_launches(1);
             return FFTSEG_OK;
@@ -291,6 +327,12 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
     p->flags = flags;
     if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
     else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
+    e = cudaMalloc((void **)&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_error(e, "cudaMalloc(status flag)");
+    }
     int rc = precision == FFTSEG_PREC_FP32 ? build_fp32(p) : tc_plan_create(p);
     if (rc != FFTSEG_OK) {
         free_plan(p);
@@ -343,6 +385,19 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
     info[3] = p->work ? p->work_segs * p->n * 8 : 0;
     info[4] = p->work_segs;
     info[5] = launches_per_exec(p, p->batch);
+    return FFTSEG_OK;
+}
+
+int fftseg_plan_check(fftseg_plan p)
+{
+    if (!p) return set_error(FFTSEG_E_INVALID, "plan_check: NULL plan");
+    int flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_error(e, "plan_check");
+    if (flag) {
+        cudaMemset(p->d_err, 0, sizeof(int));
+        return set_error(FFTSEG_E_TIMEOUT, "a kernel gave up (flag %d): a bounded wait ran out or a shared buffer was misaligned", flag);
+    }
     return FFTSEG_OK;
 }
 

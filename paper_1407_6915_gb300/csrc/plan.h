@@ -1,5 +1,6 @@
 // Plan object and host helpers shared by the library's translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,14 +28,15 @@ struct fftseg_plan_s {
     int log_n1 = 0, log_n2 = 0, log_c = 0;
     float scale = 1.f;
     // twiddle tables (device, forward values w = exp(-2 pi i m / M))
-    float2 *twA = nullptr;   // w_{n1}^m (block: w_n^m)
-    float2 *twB = nullptr;   // w_{n2}^m
+    float2 *twA = nullptr;   // stage twiddle tables of the column (block: whole) transform
+    float2 *twB = nullptr;   // stage twiddle tables of the row transform
     float2 *tw4a = nullptr;  // four-step twiddles, rows k1 mod 2^tw_log_k
     float2 *tw4b = nullptr;  // rows k1 >> tw_log_k (null when one table is exact)
     int tw_log_k = 0;
     // two-pass workspace
     float2 *work = nullptr;
     int64_t work_segs = 0;
+    int *d_err = nullptr;  // set by kernels whose bounded waits ran out
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
     fftseg::TcPlan *tc = nullptr;
@@ -46,6 +48,11 @@ namespace fftseg {
 int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 void count_launches(int64_t k);
+
+// Tensor map over 8-byte elements: dims (d0 innermost, d1, d2), byte strides
+// of dims 1 and 2, box (box0, box1, 1).
+int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1);
 
 // Run the plan on nseg segments (arguments already validated).
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);

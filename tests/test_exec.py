@@ -37,6 +37,7 @@ def run(plan, x_np, nseg=None):
     x = torch.from_numpy(x_np).cuda()
     y = plan.exec(x, nseg=nseg)
     torch.cuda.synchronize()
+    plan.check()  # no kernel gave up a bounded wait
     return y.cpu().numpy()
 
 
