@@ -287,6 +287,39 @@ FDEV void st_cluster_v2(uint32_t addr, float2 v)
     asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
 }
 
+// Remote store into CTA-shared memory of a cluster peer that also credits 8
+// bytes to the peer's mbarrier (st.async): the receiver learns of the data by
+// waiting on its own barrier; no release fence is needed on the sender side.
+FDEV void st_async_v2(uint32_t remote_addr, float2 v, uint32_t remote_bar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];" ::"r"(
+                     remote_addr),
+                 "f"(v.x), "f"(v.y), "r"(remote_bar)
+                 : "memory");
+}
+
+// Bulk copy from this CTA's shared memory to a cluster peer's shared memory
+// (both addresses 16-byte aligned, bytes % 16 == 0), completing on the peer's
+// mbarrier.  dst and bar are shared::cluster addresses (mapa).
+FDEV void dsmem_bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "r"(smem_u32(src)), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+FDEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// wait until every committed bulk copy of this thread has finished reading its source
+FDEV void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// Cluster-wide execution barrier without memory ordering (arrive.relaxed):
+// used where every thread has already consumed what it read.
+FDEV void cluster_sync_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
 FDEV bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {
     uint32_t ok;

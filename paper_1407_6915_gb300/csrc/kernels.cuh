@@ -52,6 +52,21 @@ FDEV void scatter_last(const float2 *v, Put &&put)
     }
 }
 
+// As scatter_last, also passing the butterfly slot b of the calling thread.
+template <int LOG_L, int LOG_W, bool CFAST, int T, class Put>
+FDEV void scatter_last_b(const float2 *v, Put &&put)
+{
+    using I = StageInfo<LOG_L, StageInfo<LOG_L, 0>::NSTAGES - 1>;
+    constexpr int V = (1 << (LOG_L + LOG_W)) / T, B = V / I::R;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        int c, j;
+        butterfly_coords<LOG_L, LOG_W, CFAST, I::LOG_R>(threadIdx.x + T * b, c, j);
+#pragma unroll
+        for (int r = 0; r < I::R; ++r) put(b, c, j + (r << (LOG_L - I::LOG_R)), v[b * I::R + r]);
+    }
+}
+
 // Run stages STAGE..last on the values in v (this stage's inputs).  Between
 // stages the tile goes through shared memory `sm` (layout smem_slot<..., PS>).
 // After the last butterflies the outputs stay in v for the caller.  IN_SM:
@@ -273,29 +288,52 @@ struct ClusterShape {
     static constexpr int PSB = LOG_WB < 4 ? 4 : LOG_WB;
     static constexpr int SLOTS_A = smem_slots<LOG_N1, LOG_WA, PSA>();
     static constexpr int SLOTS_B = smem_slots<LOG_N2, LOG_WB, PSB>();
-    static constexpr int SLOTS = ((SLOTS_A > SLOTS_B ? SLOTS_A : SLOTS_B) + 1) & ~1;
-    static constexpr size_t SMEM = (size_t)(SLOTS + 2 * E) * sizeof(float2) + 2 * sizeof(uint64_t);
+    // one source CTA's part of a receiver's row-pass buffer: WA*WB points plus pads
+    static constexpr int Q = 1 << (LOG_WA + LOG_WB);
+    static constexpr int SLICE = Q + (Q >> PSB);
+    static constexpr int SEND = C * SLICE;
+    static constexpr int SLOTS_S = ((SLOTS_A > SEND ? SLOTS_A : SEND) + 1) & ~1;
+    static constexpr int SLOTS_X = (SLOTS_B + 1) & ~1;
+    static constexpr int R_LAST = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>::R;
+    // P (prefetch tile) | S (column-pass scratch, then send staging) | X (row pass) | TR | barriers
+    static constexpr size_t SMEM =
+        (size_t)(E + SLOTS_S + SLOTS_X + R_LAST * (1 << LOG_WA)) * sizeof(float2) + 2 * sizeof(uint64_t);
     static constexpr int MINB = T <= 256 ? 2 : 1;  // CTAs per SM the register budget must allow
 };
 
 // One cluster of C CTAs per segment, persistent over segments
-// s = cluster, cluster + nclusters, ...  CTA r of the cluster receives the
-// column slab j2 in [r*WA, (r+1)*WA) of the next segment (N1 rows of WA
-// points) by one tiled TMA copy while it works on the current one.
+// s = cluster, cluster + nclusters, ...  CTA r of the cluster owns the column
+// slab j2 in [r*WA, (r+1)*WA) (N1 rows of WA points) in the column pass and
+// the rows k1 in [r*WB, (r+1)*WB) in the row pass.
+//  - The slab of the next segment arrives by one tiled TMA copy, issued as
+//    soon as the current slab has been read into registers.
+//  - The column-pass results, times the four-step twiddle, are laid out in S
+//    exactly as each receiver's row-pass buffer X wants them (one slice per
+//    receiver) and go out as C bulk shared-to-shared copies that complete on
+//    the receiver's barrier `rbar`; a relaxed cluster barrier first makes sure
+//    no receiver still reads its X.
+//  - Four-step twiddle w_n^{j2 k1} with k1 = j + (N1/R)*q (j = butterfly
+//    index of the last column stage): w_n^{j2 j} (per thread, kept in
+//    registers) times w_n^{j2 (N1/R) q} (table TR in shared memory), both
+//    exact table entries.
 template <int LOG_N1, int LOG_N2, int LOG_C, int S>
 __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, ClusterShape<LOG_N1, LOG_N2, LOG_C>::MINB)
     k_cluster(const __grid_constant__ ClusterArgs a)
 {
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
-    constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2, T = Sh::T, E = Sh::E;
+    constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2, T = Sh::T, E = Sh::E, C = Sh::C;
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
     constexpr int64_t N = (int64_t)N1 * N2;
+    constexpr int LOG_STEP = LOG_N1 - StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>::LOG_R;  // log2(N1/R)
     // tiled TMA writes need a 128-byte aligned destination: the prefetch
-    // buffers come first (base 1024-byte aligned, each a multiple of 1024 bytes)
+    // tile comes first (base 1024-byte aligned, a multiple of 1024 bytes)
     extern __shared__ __align__(1024) float2 sm[];
     float2 *P = sm;
-    float2 *X = sm + 2 * E;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
+    float2 *Sb = P + E;
+    float2 *X = Sb + Sh::SLOTS_S;
+    float2 *TR = X + Sh::SLOTS_X;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(TR + Sh::R_LAST * WA);  // TMA tile arrived
+    uint64_t *rbar = bar + 1;                                            // row-pass slices arrived
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x;
@@ -304,47 +342,71 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
         return;
     }
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        mbar_init(bar, 1);
+        mbar_init(rbar, 1);
         fence_mbar_init();
     }
-    __syncthreads();
+    for (int e = tid; e < Sh::R_LAST * WA; e += T)  // TR[q][c] = w_n^{(rank*WA + c) (N1/R) q}
+        TR[e] = __ldg(a.tw4 + (int64_t)((e >> Sh::LOG_WA) << LOG_STEP) * N2 + rank * WA + (e & (WA - 1)));
+    // w_n^{j2 j} for this thread's butterflies of the last column stage
+    float2 wbase[(E / T) / Sh::R_LAST];
+    {
+        using IL = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>;
+#pragma unroll
+        for (int b = 0; b < (E / T) / IL::R; ++b) {
+            int c, j;
+            butterfly_coords<LOG_N1, Sh::LOG_WA, true, IL::LOG_R>(tid + T * b, c, j);
+            wbase[b] = __ldg(a.tw4 + (int64_t)j * N2 + rank * WA + c);
+        }
+    }
+    cl.sync();  // every peer's barriers are initialised before any copy reaches them
+    const uint32_t x_remote0 = smem_u32(X) + (uint32_t)(rank * Sh::SLICE * sizeof(float2));
 
-    auto issue = [&](int64_t s, int b) {
+    auto issue = [&](int64_t s) {
         if (tid == 0) {
             fence_proxy_async();
-            mbar_expect_tx(&bar[b], (uint32_t)(E * sizeof(float2)));
-            tma_load_3d(P + b * E, &a.tmap, rank * WA, 0, (int)s, &bar[b]);
+            mbar_expect_tx(&bar[0], (uint32_t)(E * sizeof(float2)));
+            tma_load_3d(P, &a.tmap, rank * WA, 0, (int)s, &bar[0]);
         }
     };
 
-    uint32_t xrank[Sh::C];  // X of every CTA of the cluster, as shared::cluster addresses
-#pragma unroll
-    for (int q = 0; q < Sh::C; ++q) xrank[q] = mapa_u32(smem_u32(X), q);
-
     const int64_t cid = blockIdx.x >> LOG_C, ncl = gridDim.x >> LOG_C;
     int64_t s = cid;
-    if (s < a.nseg) issue(s, 0);
+    if (s < a.nseg) issue(s);
     const float scale = a.scale;
     for (int k = 0; s < a.nseg; s += ncl, ++k) {
-        const int b = k & 1;
-        if (s + ncl < a.nseg) issue(s + ncl, b ^ 1);
-        mbar_wait(&bar[b], (k >> 1) & 1, a.err);
-        const float2 *Pb = P + b * E;
+        if (tid == 0) {
+            mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
+            bulk_wait_read_all();  // the previous segment's outgoing copies no longer read S
+        }
+        mbar_wait(&bar[0], k & 1, a.err);
         float2 v[16];
 
         // column pass: line c is column j2 = rank*WA + c, points j1 = i
-        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return Pb[i * WA + c]; });
-        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, false>(v, X, a.twA);
+        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return P[i * WA + c]; });
+        __syncthreads();  // P fully read (refill it) and S free
+        if (s + ncl < a.nseg) issue(s + ncl);
+        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, false>(v, Sb, a.twA);
+        __syncthreads();  // S no longer read as column-pass scratch
 
-        cl.sync();  // every CTA of the cluster is done with its own X
-        scatter_last<LOG_N1, Sh::LOG_WA, true, T>(v, [&](int c, int k1, float2 x) {
-            const int j2 = rank * WA + c;
-            x = twmul<S>(x, __ldg(a.tw4 + k1 * N2 + j2));
-            const uint32_t slot = smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(k1 & (WB - 1), j2);
-            st_cluster_v2(xrank[k1 >> Sh::LOG_WB] + slot * (uint32_t)sizeof(float2), x);
+        // send staging: slice d of S holds, for receiver d, element
+        // (k1, j2) at q' = (j2 - rank*WA)*WB + (k1 mod WB), padded as in X
+        scatter_last_b<LOG_N1, Sh::LOG_WA, true, T>(v, [&](int b, int c, int k1, float2 x) {
+            const float2 w = TR[(k1 >> LOG_STEP) * WA + c];  // k1 = j + (N1/R) q
+            const float2 wb = wbase[b];
+            x = twmul<S>(x, make_float2(w.x * wb.x - w.y * wb.y, w.x * wb.y + w.y * wb.x));
+            const int qq = c * WB + (k1 & (WB - 1));
+            Sb[(k1 >> Sh::LOG_WB) * Sh::SLICE + qq + (qq >> Sh::PSB)] = x;
         });
-        cl.sync();  // every row this CTA owns has arrived
+        fence_proxy_async();      // these generic writes are read by the async-proxy copies below
+        __syncthreads();          // S complete
+        cluster_sync_relaxed();   // no receiver still reads its X
+        if (tid < C) {
+            dsmem_bulk_copy(mapa_u32(x_remote0, tid), Sb + tid * Sh::SLICE, Sh::SLICE * sizeof(float2),
+                            mapa_u32(smem_u32(rbar), tid));
+            bulk_commit();
+        }
+        mbar_wait(rbar, k & 1, a.err);  // every slice of this CTA's rows has arrived
 
         // row pass: line c is row k1 = rank*WB + c, points j2 = i
         gather<LOG_N2, Sh::LOG_WB, true, T, 0>(
@@ -359,7 +421,8 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             else static_cast<float2 *>(a.out)[o] = x;
         });
     }
-    cl.sync();  // no CTA leaves while a peer could still write into its X
+    if (tid < C) bulk_wait_read_all();
+    cl.sync();  // no CTA leaves while a peer could still copy into its X
 }
 
 }  // namespace fftseg
