@@ -1,0 +1,331 @@
+"""Benchmark of the segmented FFT on one or more GB300s (one process per GPU).
+
+Default workload: a resident 2^30-sample complex64 signal (8 GiB) cut into
+16384 segments of 65536 points; one step = forward transform (no scaling)
+then inverse transform (1/n) of every segment, i.e. two batched transforms.
+The signal is 32 off-bin complex tones (amplitudes log-uniform 1e-3..1) plus
+complex Gaussian noise (sigma 0.1), seed 1, synthesised on the host.
+
+Metric: GFLOP/s by the 5*n*log2(n) convention per transformed segment,
+whole job (all GPUs).  Every buffer is 8 GiB, far larger than L2, so no L2
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle (the reference arm of this
+build: the paper has no code) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 1 << 16
+SEGMENTS = 16384
+SEED = 1
+METRIC = "segment-FFT GFLOP/s and % HBM roofline, FP32 vs TC split; serve p50/p99 ms"
+UNIT = "GFLOP/s"
+WORKLOAD = "resident 8 GiB complex64 signal, 16384 segments x 65536 points, forward then inverse (1/n)"
+
+
+def flops_per_transform(n, segments):
+    return 5.0 * n * math.log2(n) * segments
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = []
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"unavailable": "nvidia-smi gave no samples"}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(seconds_target=12.0):
+    """The FP64 oracle as it stands, timed on this host's cores on a sample of the workload."""
+    import numpy as np
+    import oracle
+    import siggen
+    cores = os.cpu_count() or 1
+    seg = max(cores, 8)
+    x = siggen.tones(SEED, seg * N).reshape(seg, N)
+    t0 = time.perf_counter()
+    X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
+    oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(seconds_target / max(dt, 1e-3)))
+    reps = min(reps, 64)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
+        oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = 2 * flops_per_transform(N, seg * reps) / dt / 1e9
+    return {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of the 16384 segments, forward+inverse, %d repetitions, %.1f s wall"
+                      % (seg, reps, dt)}
+
+
+def kernel_rev():
+    """Hash of the CUDA sources: a DRAM-traffic figure only applies to the build it was taken on."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_1407_6915_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(key):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the committed ncu
+    summary (profiles/dram_traffic.txt: `<path>:<n> <bytes per launch> <kernel rev>`),
+    or None when it was taken on other kernel sources."""
+    try:
+        rev = kernel_rev()
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and parts[0] == key and parts[2] == rev:
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import numpy as np
+    import oracle
+    import siggen
+    cores = os.cpu_count() or 1
+    seg = max(cores // 2, 4)  # a bounded sample per step: a few seconds of CPU work
+    x = siggen.tones(SEED, seg * N).reshape(seg, N)
+    for _ in range(args.warmup):
+        X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
+        oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
+        oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = 2 * flops_per_transform(N, seg) * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": N, "segments": SEGMENTS,
+                       "sample_per_step": seg, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d segments forward+inverse per step" % seg},
+            "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import paper_1407_6915_gb300 as fs
+    import siggen
+
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+
+    # ---- inputs: synthesised on the host straight into pinned memory
+    h_in = torch.empty(SEGMENTS * N, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_TONES, SEED, 0, SEGMENTS * N, h_in.data_ptr())
+    h_out = torch.empty(SEGMENTS * N, dtype=torch.complex64, pin_memory=True)
+    x = h_in.to(dev).view(SEGMENTS, N)
+    y = torch.empty_like(x)
+    z = torch.empty_like(x)
+    fwd = fs.Plan(N, SEGMENTS, fs.FORWARD, fs.NORM_NONE)
+    inv = fs.Plan(N, SEGMENTS, fs.INVERSE, fs.NORM_BACKWARD)
+
+    def step():
+        fwd.exec_ptr(x.data_ptr(), y.data_ptr(), SEGMENTS, stream)
+        inv.exec_ptr(y.data_ptr(), z.data_ptr(), SEGMENTS, stream)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    fwd.check()
+    inv.check()
+
+    # ---- timed region: K steps, events around every launch for the roofline
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    e_start, e_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = fs.launch_count()
+    with Clocks(local) as clk:
+        barrier()
+        e_start.record(stream)
+        for i in range(args.steps):
+            a, b, c = evs[i]
+            a.record(stream)
+            fwd.exec_ptr(x.data_ptr(), y.data_ptr(), SEGMENTS, stream)
+            b.record(stream)
+            inv.exec_ptr(y.data_ptr(), z.data_ptr(), SEGMENTS, stream)
+            c.record(stream)
+        e_end.record(stream)
+        barrier()
+    launches = fs.launch_count() - launches0
+    ms = e_start.elapsed_time(e_end)
+    kernel_ms = [a.elapsed_time(b) for a, b, _ in evs] + [b.elapsed_time(c) for _, b, c in evs]
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    flops_step = 2 * flops_per_transform(N, SEGMENTS)
+    value = world * flops_step / (ms_per_step / 1e3) / 1e9
+
+    # round-trip check of this very run (inverse(forward(x)) == x up to rounding)
+    err = float(torch.linalg.vector_norm((z - x).flatten()) / torch.linalg.vector_norm(x.flatten()))
+
+    # ---- roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
+    peak, peak_kind = peaks()
+    per_launch_ms = statistics.mean(kernel_ms)
+    algo_bytes = 16.0 * N * SEGMENTS
+    achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
+    traffic = measured_traffic("%s:%d" % (fwd.info()["path"], N))
+
+    # ---- end to end through the public API with host buffers
+    e2e_steps = max(1, min(args.steps, 3))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        x.view(-1).copy_(h_in, non_blocking=True)
+        step()
+        h_out.copy_(z.view(-1), non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_value = world * flops_step / e2e_s / 1e9
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N, "segments": SEGMENTS, "path": fwd.info()["path"],
+                           "signal": "32 off-bin tones (log-uniform 1e-3..1) + complex Gaussian noise sigma 0.1, seed 1",
+                           "l2": "inputs larger than L2 (8 GiB per buffer), no flush needed",
+                           "replicas": "one independent replica per GPU (no collective on the data path)"},
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "traffic": traffic,
+                             "peak_kind": peak_kind,
+                             "kernel": "single-pass segment FFT (one launch per transform)",
+                             "algorithmic_bytes_per_launch": algo_bytes,
+                             "mean_launch_ms": round(per_launch_ms, 4)},
+                "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
+                        "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2)},
+                "gpu_launches": int(launches),
+                "clocks": clk.summary(),
+                "round_trip_rel_l2": err}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -63,7 +63,9 @@ enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
 
 /* plan flags */
 #define FFTSEG_FLAG_ZERO_PAD 0x1u     /* fftseg_stream: zero-pad a trailing partial segment */
-#define FFTSEG_FLAG_FORCE_TWOPASS 0x2u /* use the two-pass four-step path even where one pass fits */
+#define FFTSEG_FLAG_FORCE_TWOPASS 0x2u /* use the non-persistent two-pass path (n >= 2^8) */
+#define FFTSEG_FLAG_FOURSTEP_L2 0x4u   /* use the persistent four-step path with an L2-resident
+                                          intermediate (n = 2^14..2^24) */
 /* single-pass cluster path: request a cluster of 2^c CTAs (0 = the library's choice) */
 #define FFTSEG_FLAG_CLUSTER_LOG2(c) (((unsigned)(c) & 0xFu) << 8)
 
@@ -132,7 +134,8 @@ int fftseg_stream_phases(fftseg_plan p, double out[6]);
 
 int fftseg_plan_destroy(fftseg_plan p);
 
-/* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core),
+/* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core,
+ * 4 persistent four-step),
  * info[1] n1, info[2] n2, info[3] workspace bytes, info[4] segments per
  * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
 int fftseg_plan_info(fftseg_plan p, int64_t info[6]);

@@ -246,6 +246,14 @@ FDEV void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;
 // later async-proxy (TMA) accesses
 FDEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// order this thread's generic-proxy view of global memory (e.g. data another
+// CTA published with a release) before its later async-proxy (TMA) reads
+FDEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
+
+// Drop a 128-byte line from L2 without writing it back (its contents become
+// undefined): for intermediate data that has been consumed.
+FDEV void discard_l2_line(const void *p) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory"); }
+
 FDEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)

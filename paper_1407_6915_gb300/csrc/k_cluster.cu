@@ -60,7 +60,7 @@ bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_
         case 15: *log_n1 = 7; *log_n2 = 8; *log_c = 3; return log_c_req == 0 || log_c_req == 3;
         case 16:
             *log_n1 = 8; *log_n2 = 8;
-            *log_c = log_c_req == 4 ? 4 : 3;
+            *log_c = log_c_req == 3 ? 3 : 4;
             return log_c_req == 0 || log_c_req == 3 || log_c_req == 4;
         case 17: *log_n1 = 8; *log_n2 = 9; *log_c = 4; return log_c_req == 0 || log_c_req == 4;
         default: return false;

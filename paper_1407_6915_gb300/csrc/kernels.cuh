@@ -23,7 +23,17 @@ namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------- stage runner
 
-template <int LOG_L, int LOG_W, bool CFAST, int T, int STAGE, class Get>
+// Thread -> butterfly coordinates of stage STAGE.  CFAST tiles put lanes
+// along the lines; with JLAST the last stage instead puts lanes along the
+// points of a line (the shared-memory layout does not change).
+template <int LOG_L, int LOG_W, bool CFAST, bool JLAST, int STAGE>
+FDEV void stage_coords(int g, int &c, int &j)
+{
+    using I = StageInfo<LOG_L, STAGE>;
+    butterfly_coords<LOG_L, LOG_W, CFAST && !(JLAST && I::LAST), I::LOG_R>(g, c, j);
+}
+
+template <int LOG_L, int LOG_W, bool CFAST, int T, int STAGE, bool JLAST = false, class Get>
 FDEV void gather(float2 *v, Get &&get)
 {
     using I = StageInfo<LOG_L, STAGE>;
@@ -31,22 +41,23 @@ FDEV void gather(float2 *v, Get &&get)
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         int c, j;
-        butterfly_coords<LOG_L, LOG_W, CFAST, I::LOG_R>(threadIdx.x + T * b, c, j);
+        stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
 #pragma unroll
         for (int r = 0; r < I::R; ++r) v[b * I::R + r] = get(c, j + (r << (LOG_L - I::LOG_R)));
     }
 }
 
 // Hand every output of the last stage, (line c, index i), to put().
-template <int LOG_L, int LOG_W, bool CFAST, int T, class Put>
+template <int LOG_L, int LOG_W, bool CFAST, int T, bool JLAST = false, class Put>
 FDEV void scatter_last(const float2 *v, Put &&put)
 {
-    using I = StageInfo<LOG_L, StageInfo<LOG_L, 0>::NSTAGES - 1>;
+    constexpr int LASTS = StageInfo<LOG_L, 0>::NSTAGES - 1;
+    using I = StageInfo<LOG_L, LASTS>;
     constexpr int V = (1 << (LOG_L + LOG_W)) / T, B = V / I::R;
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         int c, j;
-        butterfly_coords<LOG_L, LOG_W, CFAST, I::LOG_R>(threadIdx.x + T * b, c, j);
+        stage_coords<LOG_L, LOG_W, CFAST, JLAST, LASTS>(threadIdx.x + T * b, c, j);
 #pragma unroll
         for (int r = 0; r < I::R; ++r) put(c, j + (r << (LOG_L - I::LOG_R)), v[b * I::R + r]);
     }
@@ -72,7 +83,7 @@ FDEV void scatter_last_b(const float2 *v, Put &&put)
 // After the last butterflies the outputs stay in v for the caller.  IN_SM:
 // this stage's inputs were read from `sm` (so a barrier must separate those
 // reads from the writes below).
-template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true>
+template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true, bool JLAST = false>
 FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
 {
     using I = StageInfo<LOG_L, STAGE>;
@@ -80,7 +91,7 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
 #pragma unroll
     for (int b = 0; b < B; ++b) {
         int c, j;
-        butterfly_coords<LOG_L, LOG_W, CFAST, I::LOG_R>(threadIdx.x + T * b, c, j);
+        stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
         butterfly<LOG_L, STAGE, S>(v + b * I::R, j, twL);
     }
     if constexpr (!I::LAST) {
@@ -88,16 +99,16 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             int c, j;
-            butterfly_coords<LOG_L, LOG_W, CFAST, I::LOG_R>(threadIdx.x + T * b, c, j);
+            stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
 #pragma unroll
             for (int r = 0; r < I::R; ++r)
                 sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, stockham_out_index<LOG_L, STAGE>(j, r))] =
                     v[b * I::R + r];
         }
         __syncthreads();
-        gather<LOG_L, LOG_W, CFAST, T, STAGE + 1>(
+        gather<LOG_L, LOG_W, CFAST, T, STAGE + 1, JLAST>(
             v, [&](int c, int i) { return sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, i)]; });
-        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1>(v, sm, twL);
+        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST>(v, sm, twL);
     }
 }
 

@@ -25,4 +25,10 @@ cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a,
 // Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
 bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
 
+// Persistent two-pass four-step kernel (L2-resident intermediate), n = 2^14..2^24.
+struct FourStepArgs;
+cudaError_t launch_fourstep(int log_n, int sign, const FourStepArgs &a, cudaStream_t st);
+// Factorisation and tile widths used for n.
+bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
+
 }  // namespace fftseg

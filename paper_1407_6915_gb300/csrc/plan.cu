@@ -6,6 +6,7 @@
 
 #include <vector>
 
+#include "fourstep.cuh"
 #include "launch.h"
 #include "plan.h"
 
@@ -18,6 +19,8 @@ std::atomic<int64_t> g_launches{0};
 constexpr int64_t kWorkTargetBytes = 32ll << 20;  // two-pass chunk: stays resident in L2
 constexpr int kTwoLevelAbove = 20;                 // n > 2^20: four-step table split in two
 constexpr int kTwLogK = 6;
+constexpr int64_t kChunkBytes = 16ll << 20;  // four-step chunk; the ring holds kRingNr of them
+constexpr int kRingNr = 3;
 
 bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 int ilog2(int64_t n)
@@ -108,13 +111,60 @@ void free_plan(fftseg_plan p)
     cudaFree(p->tw4b);
     cudaFree(p->work);
     cudaFree(p->d_err);
+    cudaFree(p->ring);
+    cudaFree(p->ctr);
+    cudaFree(p->w4);
+    cudaFree(p->w4hi);
     if (p->tc) tc_plan_destroy(p);
     delete p;
+}
+
+// Persistent four-step: ring, counters, stage tables and the transposed
+// four-step table [j2][k1] (split in two for n > 2^20).
+int build_fourstep(fftseg_plan p)
+{
+    int l1, l2, lwa, lwb;
+    if (!fourstep_shape(p->log_n, &l1, &l2, &lwa, &lwb))
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: the four-step path needs n in [2^14, 2^24]");
+    p->path = PATH_FOURSTEP;
+    p->log_n1 = l1;
+    p->log_n2 = l2;
+    p->log_wa = lwa;
+    p->log_wb = lwb;
+    const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+    int rc;
+    if ((rc = stage_table(&p->twA, n1))) return rc;
+    if ((rc = stage_table(&p->twB, n2))) return rc;
+    p->w4_log_k = p->log_n > kTwoLevelAbove ? kTwLogK : l1;
+    const int64_t K = int64_t(1) << p->w4_log_k;
+    {
+        std::vector<float2> h((size_t)(n2 * K));
+        for (int64_t j2 = 0; j2 < n2; ++j2) host_roots(h.data() + j2 * K, K, p->n, j2);
+        if ((rc = upload(&p->w4, h))) return rc;
+    }
+    if (K < n1) {
+        std::vector<float2> h((size_t)(n2 * (n1 / K)));
+        for (int64_t j2 = 0; j2 < n2; ++j2) host_roots(h.data() + j2 * (n1 / K), n1 / K, p->n, j2 * K);
+        if ((rc = upload(&p->w4hi, h))) return rc;
+    }
+    int64_t cs = kChunkBytes / (p->n * 8);
+    if (cs < 1) cs = 1;
+    if (cs > p->batch) cs = p->batch;
+    p->ring_cs = (int)cs;
+    p->ring_nr = kRingNr;
+    cudaError_t e = cudaMalloc((void **)&p->ring, (size_t)(p->ring_nr * cs * p->n) * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(ring)");
+    const int64_t nc = (p->batch + cs - 1) / cs;
+    p->ctr_count = 1 + 2 * nc;
+    e = cudaMalloc((void **)&p->ctr, (size_t)p->ctr_count * sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(counters)");
+    return FFTSEG_OK;
 }
 
 int build_fp32(fftseg_plan p)
 {
     const int ln = p->log_n;
+    if (p->flags & FFTSEG_FLAG_FOURSTEP_L2) return build_fourstep(p);
     const bool force2 = (p->flags & FFTSEG_FLAG_FORCE_TWOPASS) && ln >= 8;
     int rc;
     if (ln <= 12 && !force2) {
@@ -125,6 +175,9 @@ int build_fp32(fftseg_plan p)
     }
     int l1, l2, lc;
     const int want_c = (int)((p->flags >> 8) & 0xFu);
+    // measured on GB300: the cluster path wins up to 2^16, the persistent
+    // four-step above (a 16-CTA cluster per 2^17 segment leaves SMs idle)
+    if (!force2 && want_c == 0 && ln >= 17) return build_fourstep(p);
     if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: no cluster of 2^%d CTAs is built for n=2^%d",
                          want_c, ln);
@@ -168,6 +221,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_BLOCK:
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
+        case PATH_FOURSTEP: return 1;
         default: return tc_launches_per_exec(p);
     }
 }
@@ -279,6 +333,38 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             }
             return FFTSEG_OK;
         }
+        case PATH_FOURSTEP: {
+            FourStepArgs a{};
+            const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
+            const uint32_t boxa = (uint32_t)(n1 < 256 ? n1 : 256), boxb = (uint32_t)(n2 < 256 ? n2 : 256);
+            int rc = encode_tmap_3d(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, 1u << p->log_wa, boxa);
+            if (rc != FFTSEG_OK) return rc;
+            rc = encode_tmap_3d(&a.tmB, p->ring, n1, n2, (int64_t)p->ring_nr * p->ring_cs, n1 * 8, n * 8,
+                                1u << p->log_wb, boxb);
+            if (rc != FFTSEG_OK) return rc;
+            const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+            a.out = d_out;
+            a.ring = p->ring;
+            a.twA = p->twA;
+            a.twB = p->twB;
+            a.w4 = p->w4;
+            a.w4hi = p->w4hi;
+            a.ctr = p->ctr;
+            a.err = p->d_err;
+            a.nseg = nseg;
+            a.nchunks = (int)nc;
+            a.cs = p->ring_cs;
+            a.nr = p->ring_nr;
+            a.log_k = p->w4_log_k;
+            a.out_power = power;
+            a.scale = p->scale;
+            e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);
+            if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+            e = launch_fourstep(p->log_n, sign, a, st);
+            if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
         case PATH_TC: return tc_exec(p, d_in, d_out, nseg, st);
         default: return set_error(FFTSEG_E_INVALID, "corrupt plan");
     }
@@ -382,8 +468,8 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
     info[0] = p->path;
     info[1] = int64_t(1) << p->log_n1;
     info[2] = p->path == PATH_BLOCK ? 1 : int64_t(1) << p->log_n2;
-    info[3] = p->work ? p->work_segs * p->n * 8 : 0;
-    info[4] = p->work_segs;
+    info[3] = p->work ? p->work_segs * p->n * 8 : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
+    info[4] = p->work ? p->work_segs : p->ring_cs;
     info[5] = launches_per_exec(p, p->batch);
     return FFTSEG_OK;
 }

@@ -11,7 +11,7 @@
 
 namespace fftseg {
 
-enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_TC = 3 };
+enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_TC = 3, PATH_FOURSTEP = 4 };
 
 struct TcPlan;  // tensor-core radix-16 state (tc.cu)
 
@@ -37,6 +37,14 @@ struct fftseg_plan_s {
     float2 *work = nullptr;
     int64_t work_segs = 0;
     int *d_err = nullptr;  // set by kernels whose bounded waits ran out
+    // persistent four-step path
+    float2 *ring = nullptr;   // ring_nr * ring_cs segments
+    int ring_nr = 0, ring_cs = 0;
+    int *ctr = nullptr;       // queue head + per-chunk counters
+    int64_t ctr_count = 0;
+    float2 *w4 = nullptr, *w4hi = nullptr;
+    int w4_log_k = 0;
+    int log_wa = 0, log_wb = 0;
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
     fftseg::TcPlan *tc = nullptr;

@@ -67,11 +67,33 @@ def test_two_pass_forced_matches_oracle(log_n, direction):
     assert rel_l2(got, ref) <= tol_fp32(n)
 
 
+@pytest.mark.parametrize("log_n,B", [(14, 67), (15, 33), (16, 37), (17, 9), (18, 9), (19, 5), (20, 5), (21, 3),
+                                     (22, 2)])
+@pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
+def test_persistent_fourstep_matches_oracle(log_n, B, direction, norm):
+    # batches that span several chunks of the ring and end in a partial chunk
+    n = 1 << log_n
+    x = siggen.tones(800 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2)
+    assert plan.info()["path"] == "four-step"
+    got = run(plan, x)
+    assert rel_l2(got, oracle.fft(x, direction, norm)) <= tol_fp32(n)
+    np.testing.assert_array_equal(run(plan, x), got)  # the dynamic schedule does not change bits
+
+
+def test_persistent_fourstep_2p24_power():
+    n = 1 << 24
+    x = siggen.uniform(824, 2 * n).reshape(2, n)
+    plan = fs.Plan(n, 2, FWD, out_kind=fs.OUT_POWER, flags=fs.FLAG_FOURSTEP_L2)
+    got = run(plan, x)
+    assert rel_l2(got, oracle.power(x)) <= 2 * tol_fp32(n)
+
+
 @pytest.mark.parametrize("log_n,B", [(18, 9), (19, 5), (20, 5), (21, 2), (22, 1)])
 def test_two_pass_large_matches_oracle(log_n, B):
     n = 1 << log_n
     x = siggen.tones(300 + log_n, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, FWD)
+    plan = fs.Plan(n, B, FWD, flags=fs.FLAG_FORCE_TWOPASS)
     info = plan.info()
     assert info["path"] == "two-pass"
     got = run(plan, x)
@@ -79,7 +101,7 @@ def test_two_pass_large_matches_oracle(log_n, B):
     assert rel_l2(got, ref) <= tol_fp32(n), info
 
 
-def test_two_pass_2p24_matches_oracle():
+def test_default_2p24_matches_oracle():
     n = 1 << 24
     x = siggen.uniform(324, n).reshape(1, n)
     plan = fs.Plan(n, 1, INV, fs.NORM_BACKWARD)
