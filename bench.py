@@ -122,12 +122,13 @@ def cpu_baseline(seconds_target=12.0):
 
 
 def kernel_rev():
-    """Hash of the CUDA sources: a DRAM-traffic figure only applies to the build it was taken on."""
+    """Hash of the kernel sources (device code): a DRAM-traffic figure only applies to
+    the kernels it was taken on."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1407_6915_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
+        if name.endswith(".cuh") or (name.startswith("k_") and name.endswith(".cu")):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:12]

@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
                 f.result()
     if todo or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcuda"]
+        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
