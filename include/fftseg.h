@@ -151,6 +151,41 @@ const char *fftseg_last_error(void);
 /* Number of kernels this library has launched in this process. */
 int64_t fftseg_launch_count(void);
 
+/*
+ * fftseg_exec_noalloc: the same batched transform as a forward/inverse plan of
+ * n points, for callers that must not allocate device memory. The paper has no
+ * counterpart.
+ *
+ * Some callers can't call cudaMalloc:
+ *   - code running under a strict device-memory budget set by its host;
+ *   - plugins whose host application owns all allocations;
+ *   - real-time processing threads, where cudaMalloc may synchronise the device
+ *     and take an unbounded time.
+ * This entry point needs no plan and calls no cudaMalloc, cudaFree or other
+ * allocating routine. Its scratch is one fixed array of about 32.5 MiB,
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits. The scratch holds:
+ *   - the L2 ring of three 8 MiB chunks;
+ *   - the chunk counters;
+ *   - the twiddle tables of the last length used.
+ *
+ *   d_in, d_out  device, 16-byte aligned, [nseg][n] complex64 (may be equal)
+ *   n            a power of two from 2^17 to 2^20; anything else returns
+ *                FFTSEG_E_UNSUPPORTED, since larger lengths do not fit the
+ *                fixed scratch
+ *   direction, norm  as for fftseg_plan_create; output is always complex
+ * Asynchronous on `stream`.
+ *
+ * Set-up: the first call on a device (with that device current) looks up the
+ * array's device address. Make that first call before any stream capture.
+ * Every call shares the one array, which keeps the last call's contents. The
+ * twiddle tables are recomputed on the device when n changes; the chunk
+ * counters are cleared at every call. Calls that overlap on the GPU (for
+ * example, on two streams) race on the array and give undefined results.
+ */
+int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int64_t nseg, int direction, int norm,
+                        fftseg_stream_t stream);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching of segment-FFT jobs of different lengths.  Jobs are
  * admitted while the bytes they touch fit the HBM budget and fewer than
