@@ -202,7 +202,7 @@ __host__ __device__ constexpr int stage_table_offset(int stage)
 // Twiddle + DFT of one butterfly held in x[0..R).  tw: the stage tables of
 // a length-L line (see StageTable).
 template <int LOG_L, int STAGE, int S>
-FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ tw)
+FDEV void apply_twiddles(float2 *x, int j, const float2 *__restrict__ tw)
 {
     using I = StageInfo<LOG_L, STAGE>;
     if constexpr (!I::FIRST) {
@@ -211,7 +211,13 @@ FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ tw)
 #pragma unroll
         for (int r = 1; r < I::R; ++r) x[r] = twmul<S>(x[r], __ldg(t + (r - 1) * I::NS));
     }
-    dft<I::R, S>(x);
+}
+
+template <int LOG_L, int STAGE, int S>
+FDEV void butterfly(float2 *x, int j, const float2 *__restrict__ tw)
+{
+    apply_twiddles<LOG_L, STAGE, S>(x, j, tw);
+    dft<StageInfo<LOG_L, STAGE>::R, S>(x);
 }
 
 // Output index of element r of butterfly j.

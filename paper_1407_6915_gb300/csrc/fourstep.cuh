@@ -81,8 +81,9 @@ FDEV bool probe(const int *p, int target)
     return v >= target;
 }
 
-template <int LOG_N1, int LOG_N2, int LOG_E, int S>
-__global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T, FourStepShape<LOG_N1, LOG_N2, LOG_E>::MINB)
+template <int LOG_N1, int LOG_N2, int LOG_E, int S, int PREC = PREC_FP32>
+__global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
+                                  PREC == PREC_FP32 ? FourStepShape<LOG_N1, LOG_N2, LOG_E>::MINB : 1)
     k_fourstep(const __grid_constant__ FourStepArgs a)
 {
     using Sh = FourStepShape<LOG_N1, LOG_N2, LOG_E>;
@@ -203,6 +204,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T, FourS
     }
     uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
     const float scale = a.scale;
+    [[maybe_unused]] TcCtx tc;
+    if constexpr (PREC != PREC_FP32) tc_init<S, PREC>(tc, P);
 
     for (int k = 0;; ++k) {
         const int b = k & 1;
@@ -224,8 +227,9 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T, FourS
             const float2 *Pb = P + b * E;
             if (valid) gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WA + cc]; });
             __syncthreads();  // P[b] read
+            if constexpr (PREC != PREC_FP32) tc.stage = P + b * E + (tid >> 5) * 512;  // operand staging
             if (valid) {
-                run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PS, 0, false, true>(v, X, a.twA);
+                run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PS, 0, false, true, PREC>(v, X, a.twA, &tc);
                 float2 *dst = a.ring + ((int64_t)(c % a.nr) * a.cs + (s - (int64_t)c * a.cs)) * N;
                 scatter_last<LOG_N1, Sh::LOG_WA, true, T, true>(v, [&](int cc, int k1, float2 x) {
                     const int j2 = ct * WA + cc;
@@ -258,8 +262,9 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T, FourS
             }
             __syncthreads();  // P[b] read: the ring buffer part is no longer needed
             if (tid == 0) atomicAdd(doneB + c, 1);
+            if constexpr (PREC != PREC_FP32) tc.stage = P + b * E + (tid >> 5) * 512;  // operand staging
             if (valid) {
-                run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PS, 0, false>(v, X, a.twB);
+                run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PS, 0, false, false, PREC>(v, X, a.twB, &tc);
                 const int64_t obase = s * N + rt * WB;
                 scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int cc, int k2, float2 x) {
                     if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
@@ -269,6 +274,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T, FourS
                 });
             }
         }
+        // P[b] (tensor-core operand staging) is refilled below
+        if constexpr (PREC != PREC_FP32) __syncthreads();
         // thread 0: make sure the next tile's copy is under way, then take one more
         if (tid == 0) {
             const int nb = b ^ 1;

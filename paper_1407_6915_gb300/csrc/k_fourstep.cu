@@ -6,11 +6,11 @@ namespace fftseg {
 
 namespace {
 
-template <int LOG_N1, int LOG_N2, int LOG_E, int S>
+template <int LOG_N1, int LOG_N2, int LOG_E, int S, int PREC = PREC_FP32>
 cudaError_t fourstep_t(const FourStepArgs &a, cudaStream_t st)
 {
     using Sh = FourStepShape<LOG_N1, LOG_N2, LOG_E>;
-    auto k = k_fourstep<LOG_N1, LOG_N2, LOG_E, S>;
+    auto k = k_fourstep<LOG_N1, LOG_N2, LOG_E, S, PREC>;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
@@ -35,6 +35,16 @@ cudaError_t fourstep_s(int sign, const FourStepArgs &a, cudaStream_t st)
     return sign < 0 ? fourstep_t<LOG_N1, LOG_N2, LOG_E, -1>(a, st) : fourstep_t<LOG_N1, LOG_N2, LOG_E, 1>(a, st);
 }
 
+template <int LOG_N1, int LOG_N2, int LOG_E>
+cudaError_t fourstep_tc(int sign, int prec, const FourStepArgs &a, cudaStream_t st)
+{
+    if (prec == PREC_FP16)
+        return sign < 0 ? fourstep_t<LOG_N1, LOG_N2, LOG_E, -1, PREC_FP16>(a, st)
+                        : fourstep_t<LOG_N1, LOG_N2, LOG_E, 1, PREC_FP16>(a, st);
+    return sign < 0 ? fourstep_t<LOG_N1, LOG_N2, LOG_E, -1, PREC_BF16>(a, st)
+                    : fourstep_t<LOG_N1, LOG_N2, LOG_E, 1, PREC_BF16>(a, st);
+}
+
 }  // namespace
 
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb)
@@ -48,8 +58,16 @@ bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_w
     return true;
 }
 
-cudaError_t launch_fourstep(int log_n, int sign, const FourStepArgs &a, cudaStream_t st)
+cudaError_t launch_fourstep(int log_n, int sign, int prec, const FourStepArgs &a, cudaStream_t st)
 {
+    if (prec != PREC_FP32) {  // tensor-core radix-16 stages: n a power of 16
+        switch (log_n) {
+            case 16: return fourstep_tc<8, 8, 12>(sign, prec, a, st);
+            case 20: return fourstep_tc<10, 10, 13>(sign, prec, a, st);
+            case 24: return fourstep_tc<12, 12, 13>(sign, prec, a, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (log_n) {
         case 14: return fourstep_s<7, 7, 12>(sign, a, st);
         case 15: return fourstep_s<8, 7, 12>(sign, a, st);

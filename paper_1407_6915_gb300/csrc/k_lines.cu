@@ -19,11 +19,11 @@ int sm_count()
     return g_sm_count;
 }
 
-template <int LOG_L, int S>
+template <int LOG_L, int S, int PREC = PREC_FP32>
 cudaError_t block_t(const BlockArgs &a, cudaStream_t st)
 {
     using B = BlockShape<LOG_L>;
-    auto k = k_block<LOG_L, S>;
+    auto k = k_block<LOG_L, S, PREC>;
     static int per_sm = 0;
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
@@ -82,8 +82,20 @@ int pass_log_w(int log_l)
 #define FFTSEG_BLOCK_CASE(LL) \
     case LL: return sign < 0 ? block_t<LL, -1>(a, st) : block_t<LL, 1>(a, st);
 
-cudaError_t launch_block(int log_n, int sign, const BlockArgs &a, cudaStream_t st)
+cudaError_t launch_block(int log_n, int sign, int prec, const BlockArgs &a, cudaStream_t st)
 {
+    if (prec != PREC_FP32) {  // tensor-core radix-16 stages: n a power of 16
+#define FFTSEG_BLOCK_TC(LL)                                                                                   \
+    case LL:                                                                                                  \
+        if (prec == PREC_FP16) return sign < 0 ? block_t<LL, -1, PREC_FP16>(a, st) : block_t<LL, 1, PREC_FP16>(a, st); \
+        return sign < 0 ? block_t<LL, -1, PREC_BF16>(a, st) : block_t<LL, 1, PREC_BF16>(a, st);
+        switch (log_n) {
+            FFTSEG_BLOCK_TC(4)
+            FFTSEG_BLOCK_TC(8)
+            FFTSEG_BLOCK_TC(12)
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (log_n) {
         FFTSEG_BLOCK_CASE(1)
         FFTSEG_BLOCK_CASE(2)

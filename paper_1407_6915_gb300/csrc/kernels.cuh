@@ -16,6 +16,7 @@
 #include <cooperative_groups.h>
 
 #include "engine.cuh"
+#include "tc.cuh"
 
 namespace fftseg {
 
@@ -83,8 +84,9 @@ FDEV void scatter_last_b(const float2 *v, Put &&put)
 // After the last butterflies the outputs stay in v for the caller.  IN_SM:
 // this stage's inputs were read from `sm` (so a barrier must separate those
 // reads from the writes below).
-template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true, bool JLAST = false>
-FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
+template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true, bool JLAST = false,
+          int PREC = PREC_FP32>
+FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, const TcCtx *tc = nullptr)
 {
     using I = StageInfo<LOG_L, STAGE>;
     constexpr int V = (1 << (LOG_L + LOG_W)) / T, B = V / I::R;
@@ -92,7 +94,14 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
     for (int b = 0; b < B; ++b) {
         int c, j;
         stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
-        butterfly<LOG_L, STAGE, S>(v + b * I::R, j, twL);
+        if constexpr (PREC != PREC_FP32 && I::R == 16) {
+            // radix-16 stages on the tensor cores (warp-collective; every
+            // lane of every warp takes this branch together)
+            apply_twiddles<LOG_L, STAGE, S>(v + b * I::R, j, twL);
+            dft16_tc<S, PREC>(v + b * I::R, *tc);
+        } else {
+            butterfly<LOG_L, STAGE, S>(v + b * I::R, j, twL);
+        }
     }
     if constexpr (!I::LAST) {
         if constexpr (IN_SM) __syncthreads();  // every thread has read this stage's inputs from sm
@@ -108,7 +117,7 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL)
         __syncthreads();
         gather<LOG_L, LOG_W, CFAST, T, STAGE + 1, JLAST>(
             v, [&](int c, int i) { return sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, i)]; });
-        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST>(v, sm, twL);
+        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST, PREC>(v, sm, twL, tc);
     }
 }
 
@@ -216,8 +225,8 @@ struct BlockShape {
     static constexpr size_t SMEM = (size_t)(SLOTS + 2 * E) * sizeof(float2) + 2 * sizeof(uint64_t);
 };
 
-template <int LOG_L, int S>
-__global__ void __launch_bounds__(256, 2) k_block(const BlockArgs a)
+template <int LOG_L, int S, int PREC = PREC_FP32>
+__global__ void __launch_bounds__(256, PREC == PREC_FP32 ? 2 : 1) k_block(const BlockArgs a)
 {
     using Sh = BlockShape<LOG_L>;
     constexpr int L = 1 << LOG_L, W = 1 << Sh::LOG_W, E = Sh::E, T = Sh::T, V = E / T;
@@ -253,6 +262,8 @@ __global__ void __launch_bounds__(256, 2) k_block(const BlockArgs a)
     int64_t u = blockIdx.x;
     if (u < a.ntiles) issue(u, 0);
     const float scale = a.scale;
+    [[maybe_unused]] TcCtx tc;
+    if constexpr (PREC != PREC_FP32) tc_init<S, PREC>(tc, P);
     for (int k = 0; u < a.ntiles; u += gridDim.x, ++k) {
         const int b = k & 1;
         if (u + gridDim.x < a.ntiles) issue(u + gridDim.x, b ^ 1);
@@ -260,7 +271,14 @@ __global__ void __launch_bounds__(256, 2) k_block(const BlockArgs a)
         const float2 *Pb = P + b * E;
         float2 v[V];
         gather<LOG_L, Sh::LOG_W, false, T, 0>(v, [&](int c, int i) { return Pb[(c << LOG_L) + i]; });
-        run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false>(v, X, a.twL);
+        if constexpr (PREC == PREC_FP32) {
+            run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false>(v, X, a.twL);
+        } else {
+            // the tensor-core stages stage their operands in the tile just read
+            __syncthreads();
+            tc.stage = P + b * E + (threadIdx.x >> 5) * 512;
+            run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false, false, PREC>(v, X, a.twL, &tc);
+        }
         const int64_t line0 = u * W;
         scatter_last<LOG_L, Sh::LOG_W, false, T>(v, [&](int c, int i, float2 x) {
             if (line0 + c >= a.nseg) return;

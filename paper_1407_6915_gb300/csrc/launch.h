@@ -9,7 +9,8 @@ namespace fftseg {
 
 // Single-pass segment-major tiles for n = 2^log_n <= 4096 (persistent CTAs,
 // a.ntiles tiles of block_segments_per_cta segments).  Returns the launch error.
-cudaError_t launch_block(int log_n, int sign, const BlockArgs &a, cudaStream_t st);
+// prec: PREC_FP32, or PREC_FP16 / PREC_BF16 (tensor-core radix-16 stages, n = 16, 256, 4096).
+cudaError_t launch_block(int log_n, int sign, int prec, const BlockArgs &a, cudaStream_t st);
 int device_sm_count();
 // Segments per CTA of the block kernel.
 int block_segments_per_cta(int log_n);
@@ -27,7 +28,8 @@ bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_
 
 // Persistent two-pass four-step kernel (L2-resident intermediate), n = 2^14..2^24.
 struct FourStepArgs;
-cudaError_t launch_fourstep(int log_n, int sign, const FourStepArgs &a, cudaStream_t st);
+// prec as for launch_block (tensor-core stages for n = 2^16, 2^20, 2^24).
+cudaError_t launch_fourstep(int log_n, int sign, int prec, const FourStepArgs &a, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 

@@ -168,7 +168,7 @@ extern "C" int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int
         a.scale = scale;
         e = cudaMemsetAsync(ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);  // queue head and chunk counters
         if (e != cudaSuccess) return cuda_error(e, "exec_noalloc: counter reset");
-        e = launch_fourstep(log_n, direction, a, st);
+        e = launch_fourstep(log_n, direction, PREC_FP32, a, st);
         if (e != cudaSuccess) return cuda_error(e, "exec_noalloc: kernel launch");
         count_launches(1);
     }

@@ -117,7 +117,6 @@ void free_plan(fftseg_plan p)
     cudaFree(p->ctr);
     cudaFree(p->w4);
     cudaFree(p->w4hi);
-    if (p->tc) tc_plan_destroy(p);
     delete p;
 }
 
@@ -161,6 +160,29 @@ int build_fourstep(fftseg_plan p)
     e = cudaMalloc((void **)&p->ctr, (size_t)p->ctr_count * sizeof(int));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(counters)");
     return FFTSEG_OK;
+}
+
+int kernel_prec(fftseg_plan p)
+{
+    return p->precision == FFTSEG_PREC_TC_FP16 ? PREC_FP16 : p->precision == FFTSEG_PREC_TC_BF16 ? PREC_BF16 : PREC_FP32;
+}
+
+// Tensor-core precisions: radix-16 stages as split hi+lo GEMMs (n a power of
+// 16): n <= 4096 on the block kernel, larger n on the persistent four-step.
+int build_tc(fftseg_plan p)
+{
+    const int ln = p->log_n;
+    if (ln % 4 != 0 || ln < 4)
+        return set_error(FFTSEG_E_UNSUPPORTED,
+                         "plan_create: the tensor-core precisions need n to be a power of 16 (16 .. 2^24)");
+    if (p->flags & FFTSEG_FLAG_FORCE_TWOPASS)
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: the tensor-core precisions have no two-pass form");
+    if (ln <= 12) {
+        p->path = PATH_BLOCK;
+        p->log_n1 = ln;
+        return stage_table(&p->twA, p->n);
+    }
+    return build_fourstep(p);
 }
 
 int build_fp32(fftseg_plan p)
@@ -224,7 +246,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
-        default: return tc_launches_per_exec(p);
+        default: return 0;
     }
 }
 
@@ -275,7 +297,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             a.err = p->d_err;
             a.out_power = power;
             a.scale = p->scale;
-            e = launch_block(p->log_n, sign, a, st);
+            e = launch_block(p->log_n, sign, kernel_prec(p), a, st);
             if (e != cudaSuccess) return cuda_error(e, "block kernel launch");
             count_launches(1);
             return FFTSEG_OK;
@@ -373,12 +395,11 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             a.scale = p->scale;
             e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);
             if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
-            e = launch_fourstep(p->log_n, sign, a, st);
+            e = launch_fourstep(p->log_n, sign, kernel_prec(p), a, st);
             if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
             count_launches(1);
             return FFTSEG_OK;
         }
-        case PATH_TC: return tc_exec(p, d_in, d_out, nseg, st);
         default: return set_error(FFTSEG_E_INVALID, "corrupt plan");
     }
 }
@@ -432,7 +453,7 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
         free_plan(p);
         return cuda_error(e, "cudaMalloc(status flag)");
     }
-    int rc = precision == FFTSEG_PREC_FP32 ? build_fp32(p) : tc_plan_create(p);
+    int rc = precision == FFTSEG_PREC_FP32 ? build_fp32(p) : build_tc(p);
     if (rc != FFTSEG_OK) {
         free_plan(p);
         return rc;

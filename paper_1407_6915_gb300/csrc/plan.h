@@ -11,9 +11,7 @@
 
 namespace fftseg {
 
-enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_TC = 3, PATH_FOURSTEP = 4 };
-
-struct TcPlan;  // tensor-core radix-16 state (tc.cu)
+enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4 };
 
 }  // namespace fftseg
 
@@ -47,7 +45,6 @@ struct fftseg_plan_s {
     int log_wa = 0, log_wb = 0;
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
-    fftseg::TcPlan *tc = nullptr;
 };
 
 namespace fftseg {
@@ -68,10 +65,5 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
 // Forward-direction roots of unity w_M^m for m < M, evaluated in double.
 void host_roots(float2 *t, int64_t count, int64_t M, int64_t stride_exp);
 
-// tensor-core path (tc.cu)
-int tc_plan_create(fftseg_plan p);
-void tc_plan_destroy(fftseg_plan p);
-int tc_exec(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);
-int64_t tc_launches_per_exec(fftseg_plan p);
 
 }  // namespace fftseg
