@@ -150,6 +150,139 @@ def measured_traffic(key):
     return None
 
 
+def tc_split(peak):
+    """FP32 versus tensor-core (split hi+lo FP16 / BF16) on the same GPU: time of one
+    4 GiB batch and relative L2 error against the FP64 oracle on a sample of segments."""
+    import torch
+    import numpy as np
+    import oracle
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    out = []
+    sample = {12: 64, 16: 8, 20: 2, 24: 1}
+    for log_n in (12, 16, 20, 24):
+        n = 1 << log_n
+        B = (1 << 29) // n
+        h = torch.empty(B * n, dtype=torch.complex64, pin_memory=True)
+        siggen.fill_pointer(siggen.KIND_UNIFORM, 3, 0, B * n, h.data_ptr())
+        x = h.cuda().view(B, n)
+        y = torch.empty_like(x)
+        k = sample[log_n]
+        ref = oracle.fft(h[:k * n].numpy().reshape(k, n), oracle.FORWARD)
+        row = {"n": n, "segments": B}
+        for name, prec in (("fp32", fs.PREC_FP32), ("tc_fp16", fs.PREC_TC_FP16), ("tc_bf16", fs.PREC_TC_BF16)):
+            plan = fs.Plan(n, B, fs.FORWARD, precision=prec)
+            for _ in range(3):
+                plan.exec(x, out=y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            reps = 5
+            for _ in range(reps):
+                plan.exec(x, out=y)
+            e1.record()
+            torch.cuda.synchronize()
+            plan.check()
+            ms = e0.elapsed_time(e1) / reps
+            got = y[:k].cpu().numpy().astype(np.complex128)
+            err = float(np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()))
+            gbs = 16.0 * n * B / (ms / 1e3) / 1e9
+            row[name] = {"ms": round(ms, 4), "gflops": round(flops_per_transform(n, B) / (ms / 1e3) / 1e9, 1),
+                         "hbm_frac": round(gbs / peak, 4), "rel_l2": err, "path": plan.info()["path"]}
+            del plan
+        out.append(row)
+        del x, y, h
+        torch.cuda.empty_cache()
+    return {"batch_bytes": 1 << 32, "input": "uniform[-1,1), seed 3",
+            "rel_l2_sample_segments": {str(1 << k): v for k, v in sample.items()},
+            "bound_fp32": "2e-6*log2(n)", "bound_tc": 1e-4, "sizes": out}
+
+
+def serve_bench(peak, njobs=600, seed=5):
+    """Poisson arrivals at 0.3/0.7/0.95 of the measured saturated throughput through the
+    continuous-batching server (32 GB budget); p50/p99 submit-to-completion latency."""
+    import concurrent.futures as cf
+    import numpy as np
+    import torch
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    rng = np.random.default_rng(seed)
+    cap = 1 << 28  # samples per job at most (2 GiB of input), so a bounded pool holds the jobs in flight
+    jobs = []
+    for _ in range(njobs):
+        e = int(rng.integers(8, 23))
+        n = 1 << e
+        nseg = max(1, int(2.0 ** rng.uniform(0, 12)))
+        nseg = max(1, min(nseg, cap // n))
+        direction = fs.FORWARD if rng.random() < 0.5 else fs.INVERSE
+        norm = fs.NORM_BACKWARD if direction == fs.INVERSE else fs.NORM_NONE
+        jobs.append((n, nseg, direction, norm))
+    x = torch.empty(cap, dtype=torch.complex64, device="cuda")
+    h = torch.empty(cap, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_UNIFORM, seed, 0, cap, h.data_ptr())
+    x.copy_(h)
+    ring_elems = 34 << 27  # 34 GiB of complex64 outputs, used round-robin
+    ring = torch.empty(ring_elems, dtype=torch.complex64, device="cuda")
+    budget = 32 << 30
+
+    def run(arrivals):
+        srv = fs.Server(hbm_budget_bytes=budget, max_inflight_jobs=256)
+        lat = [None] * len(jobs)
+        pos = 0
+        t0 = time.perf_counter()
+        with cf.ThreadPoolExecutor(max_workers=512) as ex:
+            futs = []
+            for i, (n, nseg, direction, norm) in enumerate(jobs):
+                if arrivals is not None:
+                    wait = t0 + arrivals[i] - time.perf_counter()
+                    if wait > 0:
+                        time.sleep(wait)
+                sz = n * nseg
+                if pos + sz > ring_elems:
+                    pos = 0
+                out_ptr = ring.data_ptr() + 8 * pos
+                pos += sz
+                ts = time.perf_counter()
+                jid = srv.submit(x.data_ptr(), out_ptr, n, nseg, direction, norm)
+
+                def wait_one(jid=jid, ts=ts, i=i):
+                    done, st = srv.poll(jid, timeout_us=120_000_000)
+                    lat[i] = (time.perf_counter() - ts) if (done and st == fs.OK) else None
+
+                futs.append(ex.submit(wait_one))
+            for f in futs:
+                f.result()
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+        srv.destroy()
+        return lat, wall, stats
+
+    samples = sum(n * nseg for n, nseg, _, _ in jobs)
+    flops = sum(5.0 * n * math.log2(n) * nseg for n, nseg, _, _ in jobs)
+    run(None)  # warm-up: plans, graphs, first-touch
+    _, wall_sat, _ = run(None)
+    sat_rate = samples / wall_sat  # samples/s, everything queued at once
+    loads = []
+    for load in (0.3, 0.7, 0.95):
+        lam = load * sat_rate / (samples / len(jobs))  # jobs/s
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+        lat, wall, stats = run(arrivals)
+        ok = [v for v in lat if v is not None]
+        loads.append({"offered_load": load, "offered_jobs_per_s": round(lam, 1),
+                      "p50_ms": round(1e3 * float(np.percentile(ok, 50)), 3),
+                      "p99_ms": round(1e3 * float(np.percentile(ok, 99)), 3),
+                      "throughput_gflops": round(flops / wall / 1e9, 1),
+                      "hbm_frac": round(16.0 * samples / wall / 1e9 / peak, 4),
+                      "jobs_ok": len(ok), "launches": stats["launches"],
+                      "peak_admitted_bytes": stats["peak_admitted_bytes"]})
+    del ring, x
+    torch.cuda.empty_cache()
+    return {"jobs": njobs, "budget_bytes": budget,
+            "job_recipe": "n = 2^e, e uniform in 8..22; segments 2^U(0,12) capped at 2^28 samples per job; "
+                          "50/50 forward / inverse(1/n); uniform[-1,1) input",
+            "saturated_gflops": round(flops / wall_sat / 1e9, 1),
+            "saturated_hbm_frac": round(16.0 * samples / wall_sat / 1e9 / peak, 4), "loads": loads}
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -304,6 +437,11 @@ def run_ours(args):
                 "round_trip_rel_l2": err}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
+        if world == 1 and not args.no_extras:
+            del x, y, z
+            torch.cuda.empty_cache()
+            line["tc_split"] = tc_split(peak)
+            line["serve"] = serve_bench(peak)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
@@ -320,6 +458,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the tensor-core split and the serving run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -225,6 +225,32 @@ struct BlockShape {
     static constexpr size_t SMEM = (size_t)(SLOTS + 2 * E) * sizeof(float2) + 2 * sizeof(uint64_t);
 };
 
+// One tile of whole segments, already in shared memory (Pb, dense [c][i]):
+// W segments from segment line0 on (those at or past nseg are not stored).
+// With tensor-core stages tc->stage must point into Pb (this warp's 4 KB).
+template <int LOG_L, int S, int PREC = PREC_FP32>
+FDEV void block_tile(const float2 *Pb, float2 *X, const float2 *__restrict__ twL, int64_t line0, int64_t nseg,
+                     void *out, int out_power, float scale, const TcCtx *tc)
+{
+    using Sh = BlockShape<LOG_L>;
+    constexpr int L = 1 << LOG_L, T = Sh::T, V = Sh::E / T;
+    float2 v[V];
+    gather<LOG_L, Sh::LOG_W, false, T, 0>(v, [&](int c, int i) { return Pb[(c << LOG_L) + i]; });
+    if constexpr (PREC == PREC_FP32) {
+        run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false>(v, X, twL);
+    } else {
+        __syncthreads();  // the tensor-core stages stage their operands in the tile just read
+        run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false, false, PREC>(v, X, twL, tc);
+    }
+    scatter_last<LOG_L, Sh::LOG_W, false, T>(v, [&](int c, int i, float2 x) {
+        if (line0 + c >= nseg) return;
+        if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
+        const int64_t o = (line0 + c) * L + i;
+        if (out_power) static_cast<float *>(out)[o] = power_of(x);
+        else static_cast<float2 *>(out)[o] = x;
+    });
+}
+
 template <int LOG_L, int S, int PREC = PREC_FP32>
 __global__ void __launch_bounds__(256, PREC == PREC_FP32 ? 2 : 1) k_block(const BlockArgs a)
 {
@@ -268,25 +294,8 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP32 ? 2 : 1) k_block(const 
         const int b = k & 1;
         if (u + gridDim.x < a.ntiles) issue(u + gridDim.x, b ^ 1);
         mbar_wait(&bar[b], (k >> 1) & 1, a.err);
-        const float2 *Pb = P + b * E;
-        float2 v[V];
-        gather<LOG_L, Sh::LOG_W, false, T, 0>(v, [&](int c, int i) { return Pb[(c << LOG_L) + i]; });
-        if constexpr (PREC == PREC_FP32) {
-            run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false>(v, X, a.twL);
-        } else {
-            // the tensor-core stages stage their operands in the tile just read
-            __syncthreads();
-            tc.stage = P + b * E + (threadIdx.x >> 5) * 512;
-            run_stages<LOG_L, Sh::LOG_W, false, S, T, Sh::PS, 0, false, false, PREC>(v, X, a.twL, &tc);
-        }
-        const int64_t line0 = u * W;
-        scatter_last<LOG_L, Sh::LOG_W, false, T>(v, [&](int c, int i, float2 x) {
-            if (line0 + c >= a.nseg) return;
-            if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
-            const int64_t o = (line0 + c) * L + i;
-            if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
-            else static_cast<float2 *>(a.out)[o] = x;
-        });
+        if constexpr (PREC != PREC_FP32) tc.stage = P + b * E + (threadIdx.x >> 5) * 512;
+        block_tile<LOG_L, S, PREC>(P + b * E, X, a.twL, u * W, a.nseg, a.out, a.out_power, scale, &tc);
         __syncthreads();  // P[b] fully read before it is refilled two tiles on
     }
 }

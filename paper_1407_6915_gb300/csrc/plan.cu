@@ -72,14 +72,16 @@ int upload(float2 **dst, const std::vector<float2> &h)
     return FFTSEG_OK;
 }
 
+}  // namespace
+
 // Stage twiddle tables of a length-L line, in the order the kernels read them:
 // for every stage s >= 1 (radix R_s, Ns = 16^s combined points before it),
 // entries [r-1][m] = w_{Ns R_s}^{m r}, r = 1..R_s-1, m = 0..Ns-1.  The radix
 // schedule is 16, 16, ..., then one 2/4/8 stage for the remainder.
-int stage_table(float2 **dst, int64_t L)
+void stage_table_host(std::vector<float2> &h, int64_t L)
 {
     int log_l = ilog2(L);
-    std::vector<float2> h;
+    h.clear();
     int64_t ns = 1;
     for (int left = log_l; left > 0;) {
         const int lr = left >= 4 ? 4 : left;
@@ -93,6 +95,14 @@ int stage_table(float2 **dst, int64_t L)
         left -= lr;
     }
     if (h.empty()) h.push_back(make_float2(1.f, 0.f));
+}
+
+namespace {
+
+int stage_table(float2 **dst, int64_t L)
+{
+    std::vector<float2> h;
+    stage_table_host(h, L);
     return upload(dst, h);
 }
 

@@ -6,6 +6,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "fftseg.h"
 
@@ -64,6 +65,9 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
 
 // Forward-direction roots of unity w_M^m for m < M, evaluated in double.
 void host_roots(float2 *t, int64_t count, int64_t M, int64_t stride_exp);
+
+// Stage twiddle tables of a length-L line in the kernels' layout.
+void stage_table_host(std::vector<float2> &h, int64_t L);
 
 
 }  // namespace fftseg
