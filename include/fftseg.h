@@ -66,6 +66,8 @@ enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
 #define FFTSEG_FLAG_FORCE_TWOPASS 0x2u /* use the non-persistent two-pass path (n >= 2^8) */
 #define FFTSEG_FLAG_FOURSTEP_L2 0x4u   /* use the persistent four-step path with an L2-resident
                                           intermediate (n = 2^14..2^24) */
+#define FFTSEG_FLAG_FOURSTEP_PRODUCER 0x8u /* four-step path, FP32: one producer warp feeds eight
+                                             compute warps (TMA loads and stores) */
 /* single-pass cluster path: request a cluster of 2^c CTAs (0 = the library's choice) */
 #define FFTSEG_FLAG_CLUSTER_LOG2(c) (((unsigned)(c) & 0xFu) << 8)
 

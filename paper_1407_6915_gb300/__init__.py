@@ -21,7 +21,7 @@ FORWARD, INVERSE = -1, 1
 NORM_NONE, NORM_BACKWARD, NORM_ORTHO = 0, 1, 2
 PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
 OUT_COMPLEX, OUT_POWER = 0, 1
-FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2 = 0x1, 0x2, 0x4
+FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2, FLAG_FOURSTEP_PRODUCER = 0x1, 0x2, 0x4, 0x8
 
 
 PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step"}

@@ -256,6 +256,28 @@ FDEV void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::
 // CTA published with a release) before its later async-proxy (TMA) reads
 FDEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
+// Tiled 3-D TMA store of one box from shared memory (16-byte aligned, dense
+// box layout) to `tmap` at (x, y, z); tracked by bulk groups of this thread.
+FDEV void tma_store_3d(const CUtensorMap *tmap, int x, int y, int z, const void *src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src))
+                 : "memory");
+}
+
+// wait until every committed bulk copy of this thread has completed its writes
+FDEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// wait until every committed bulk store of this thread has read its source
+FDEV void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+
+// plain arrive (count 1) on an mbarrier
+FDEV void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Drop a 128-byte line from L2 without writing it back (its contents become
 // undefined): for intermediate data that has been consumed.
 FDEV void discard_l2_line(const void *p) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory"); }

@@ -30,15 +30,15 @@ struct FourStepArgs {
     float2 *ring;           // NR*CS segments of n points, [slot*CS + sl][j2][k1]
     const float2 *twA;      // stage tables, length N1
     const float2 *twB;      // stage tables, length N2
-    const float2 *w4;       // [j2][k1 mod K] = w_n^{j2 (k1 mod K)}, K = 2^log_k
-    const float2 *w4hi;     // [j2][k1 >> log_k] = w_n^{j2 K (k1 >> log_k)}, or null when K = N1
+    const float2 *w4;       // [j2][k1 mod K] = w_n^{j2 (k1 mod K)}, K = 64 above 2^20, else N1
+    const float2 *w4hi;     // [j2][k1 >> 6] = w_n^{j2 64 (k1 >> 6)} above 2^20, else unused
     int *ctr;               // [0] queue head, [1 + c] A tiles done, [1 + NC + c] B tiles done
     int *err;
     int64_t nseg;
     int nchunks;            // NC
     int cs;                 // segments per chunk
     int nr;                 // ring buffers
-    int log_k;
+    int log_k;              // log2 K (checked against the kernel's own choice by the host)
     int out_power;
     float scale;
 };
@@ -56,9 +56,11 @@ struct FourStepShape {
     static constexpr int SLOTS_B = smem_slots<LOG_N2, LOG_WB, PS>();
     static constexpr int SLOTS = ((SLOTS_A > SLOTS_B ? SLOTS_A : SLOTS_B) + 1) & ~1;
     // P[2] (input tiles) | X (stage scratch) | 2 barriers | 2 item slots
-    static constexpr size_t SMEM = (size_t)(2 * E + SLOTS) * sizeof(float2) + 2 * sizeof(uint64_t) + 2 * sizeof(int64_t);
+    static constexpr size_t SMEM = (size_t)(2 * E + SLOTS) * sizeof(float2) + 2 * sizeof(uint64_t) + 10 * sizeof(int64_t);
     static constexpr int MINB = T <= 256 ? 2 : 1;
     static_assert(LOG_WA >= 1 && LOG_WB >= 1, "a tile row must hold at least 16 bytes");
+    // the stage exchange's barrier also orders the tile reads before the refill
+    static_assert(StageInfo<LOG_N1, 0>::NSTAGES >= 2 && StageInfo<LOG_N2, 0>::NSTAGES >= 2, "two stages per pass");
 };
 
 // bounded spin until *p >= target (acquire); false if it never got there
@@ -86,6 +88,9 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
                                   PREC == PREC_FP32 ? FourStepShape<LOG_N1, LOG_N2, LOG_E>::MINB : 1)
     k_fourstep(const __grid_constant__ FourStepArgs a)
 {
+    // four-step table: exact [j2][k1] up to n = 2^20, else two factors with K = 64
+    constexpr bool TWO_LEVEL = LOG_N1 + LOG_N2 > 20;
+    constexpr int TW_LOG_K = TWO_LEVEL ? 6 : LOG_N1;
     using Sh = FourStepShape<LOG_N1, LOG_N2, LOG_E>;
     constexpr int N1 = Sh::N1, N2 = Sh::N2, E = Sh::E, T = Sh::T;
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
@@ -95,7 +100,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
     float2 *P = sm;  // two input tiles
     float2 *X = sm + 2 * E;
     uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
-    int64_t *item = reinterpret_cast<int64_t *>(bar + 2);
+    int64_t *item = reinterpret_cast<int64_t *>(bar + 2);  // [2]: the queue item held in P[b]
+    int64_t *info = item + 2;                               // [2][4]: is_b, chunk, tile, segment
     const int tid = threadIdx.x;
     if (smem_u32(P) & 127) {
         if (tid == 0) atomicOr(a.err, 2);
@@ -130,13 +136,14 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         return (int64_t)c * a.cs + (isb ? w / TB_SEG : w / TA_SEG);
     };
     // dependency of a tile: (counter, target), or none
+    // (the counters count warps: every warp of a tile adds one when done)
     auto dep = [&](int isb, int c, const int *&p, int &target) {
         if (isb) {
             p = doneA + c;
-            target = TA;
+            target = TA * (T / 32);
         } else if (c >= a.nr) {
             p = doneB + (c - a.nr);
-            target = TB;
+            target = TB * (T / 32);
         } else {
             p = nullptr;
             target = 0;
@@ -171,6 +178,10 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         if (t >= total) return false;
         int isb, c, w;
         decode(t, isb, c, w);
+        info[4 * b] = isb;
+        info[4 * b + 1] = c;
+        info[4 * b + 2] = w;
+        info[4 * b + 3] = seg_of(isb, c, w);
         const int *p;
         int target;
         dep(isb, c, p, target);
@@ -204,6 +215,7 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
     }
     uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
     const float scale = a.scale;
+    const int warp = tid >> 5, lane = tid & 31;
     [[maybe_unused]] TcCtx tc;
     if constexpr (PREC != PREC_FP32) tc_init<S, PREC>(tc, P);
 
@@ -212,10 +224,11 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         __syncthreads();  // item[b] (and its copy) published by thread 0
         const int64_t t = item[b];
         if (t >= total) break;
-        int isb, c, w;
-        decode(t, isb, c, w);
-        const int64_t s = seg_of(isb, c, w);
+        const int isb = (int)info[4 * b], c = (int)info[4 * b + 1], w = (int)info[4 * b + 2];
+        const int64_t s = info[4 * b + 3];
         const bool valid = s < a.nseg;
+        const int slab = (c % a.nr) * a.cs + (int)(s - (int64_t)c * a.cs);  // ring slab of segment s
+        const float2 *Pb = P + b * E;
         float2 v[16];
         if (valid) {
             mbar_wait(&bar[b], (phase >> b) & 1, a.err);
@@ -224,54 +237,102 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         if (!isb) {
             // ---- A tile: columns j2 = ct*WA + cc of segment s, points j1 over N1
             const int ct = w % TA_SEG;
-            const float2 *Pb = P + b * E;
-            if (valid) gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WA + cc]; });
-            __syncthreads();  // P[b] read
-            if constexpr (PREC != PREC_FP32) tc.stage = P + b * E + (tid >> 5) * 512;  // operand staging
             if (valid) {
+                gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WA + cc]; });
+                if constexpr (PREC != PREC_FP32) {
+                    __syncthreads();  // P[b] is about to hold tensor-core operands
+                    tc.stage = P + b * E + warp * 512;
+                }
+                // (FP32: the stage exchange's barrier orders every read of P[b]
+                // before thread 0 refills it at the end of the iteration)
                 run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PS, 0, false, true, PREC>(v, X, a.twA, &tc);
-                float2 *dst = a.ring + ((int64_t)(c % a.nr) * a.cs + (s - (int64_t)c * a.cs)) * N;
-                scatter_last<LOG_N1, Sh::LOG_WA, true, T, true>(v, [&](int cc, int k1, float2 x) {
+                // last stage in line-major order: this thread's outputs are
+                // k1 = j + (N1/R) r of column j2 = ct*WA + cc
+                using IL = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>;
+                constexpr int BL = 16 / IL::R;
+#pragma unroll
+                for (int bb = 0; bb < BL; ++bb) {
+                    int cc, j;
+                    stage_coords<LOG_N1, Sh::LOG_WA, true, true, IL::NSTAGES - 1>(tid + T * bb, cc, j);
                     const int j2 = ct * WA + cc;
-                    float2 wv = __ldg(a.w4 + ((int64_t)j2 << a.log_k) + (k1 & ((1 << a.log_k) - 1)));
-                    if (a.w4hi) {
-                        const float2 w2 = __ldg(a.w4hi + (int64_t)j2 * (N1 >> a.log_k) + (k1 >> a.log_k));
-                        wv = make_float2(wv.x * w2.x - wv.y * w2.y, wv.x * w2.y + wv.y * w2.x);
+                    float2 *dst = a.ring + (int64_t)slab * N + (int64_t)j2 * N1 + j;
+                    if constexpr (TWO_LEVEL) {
+                        const float2 *w4 = a.w4 + ((int64_t)j2 << TW_LOG_K);
+                        const float2 *w4h = a.w4hi + (int64_t)j2 * (N1 >> TW_LOG_K);
+#pragma unroll
+                        for (int r = 0; r < IL::R; ++r) {
+                            const int k1 = j + r * (N1 / IL::R);
+                            const float2 w1 = __ldg(w4 + (k1 & ((1 << TW_LOG_K) - 1)));
+                            const float2 w2 = __ldg(w4h + (k1 >> TW_LOG_K));
+                            const float2 wv = make_float2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
+                            dst[r * (N1 / IL::R)] = twmul<S>(v[bb * IL::R + r], wv);
+                        }
+                    } else {
+                        const float2 *w4 = a.w4 + (int64_t)j2 * N1 + j;
+#pragma unroll
+                        for (int r = 0; r < IL::R; ++r)
+                            dst[r * (N1 / IL::R)] = twmul<S>(v[bb * IL::R + r], __ldg(w4 + r * (N1 / IL::R)));
                     }
-                    dst[(int64_t)j2 * N1 + k1] = twmul<S>(x, wv);
-                });
+                }
             }
-            __syncthreads();  // every store of this tile issued
-            if (tid == 0) {
+            // each warp publishes its part of the tile once its stores are out
+            __syncwarp();
+            if (lane == 0) {
                 __threadfence();
                 atomicAdd(doneA + c, 1);
             }
         } else {
             // ---- B tile: rows k1 = rt*WB + cc of segment s, points j2 over N2
             const int rt = w % TB_SEG;
-            const float2 *Pb = P + b * E;
             if (valid) {
                 // the tile's ring lines are in shared memory now: drop them from
                 // L2 so the consumed intermediate is never written back to HBM
                 constexpr int LINES_PER_ROW = WB * 8 / 128 > 0 ? WB * 8 / 128 : 1;
-                const float2 *tile = a.ring + ((int64_t)(c % a.nr) * a.cs + (s - (int64_t)c * a.cs)) * N + rt * WB;
+                const float2 *tile = a.ring + (int64_t)slab * N + rt * WB;
                 if (WB * 8 % 128 == 0)
                     for (int l = tid; l < N2 * LINES_PER_ROW; l += T)
                         discard_l2_line(tile + (int64_t)(l / LINES_PER_ROW) * N1 + (l % LINES_PER_ROW) * 16);
-                gather<LOG_N2, Sh::LOG_WB, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WB + cc]; });
             }
-            __syncthreads();  // P[b] read: the ring buffer part is no longer needed
-            if (tid == 0) atomicAdd(doneB + c, 1);
-            if constexpr (PREC != PREC_FP32) tc.stage = P + b * E + (tid >> 5) * 512;  // operand staging
+            // each warp releases its part of the ring buffer (its lines dropped)
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicAdd(doneB + c, 1);
+            }
             if (valid) {
+                gather<LOG_N2, Sh::LOG_WB, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WB + cc]; });
+                if constexpr (PREC != PREC_FP32) {
+                    __syncthreads();  // P[b] is about to hold tensor-core operands
+                    tc.stage = P + b * E + warp * 512;
+                }
                 run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PS, 0, false, false, PREC>(v, X, a.twB, &tc);
-                const int64_t obase = s * N + rt * WB;
-                scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int cc, int k2, float2 x) {
-                    if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
-                    const int64_t o = obase + (int64_t)k2 * N1 + cc;
-                    if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
-                    else static_cast<float2 *>(a.out)[o] = x;
-                });
+                using IL = StageInfo<LOG_N2, StageInfo<LOG_N2, 0>::NSTAGES - 1>;
+                constexpr int BL = 16 / IL::R;
+#pragma unroll
+                for (int bb = 0; bb < BL; ++bb) {
+                    int cc, j;
+                    stage_coords<LOG_N2, Sh::LOG_WB, true, false, IL::NSTAGES - 1>(tid + T * bb, cc, j);
+                    const int64_t o = s * N + rt * WB + cc + (int64_t)j * N1;  // k2 = j + (N2/R) r
+                    if (a.out_power) {
+                        float *op = static_cast<float *>(a.out) + o;
+#pragma unroll
+                        for (int r = 0; r < IL::R; ++r) {
+                            float2 x = v[bb * IL::R + r];
+                            x = make_float2(x.x * scale, x.y * scale);
+                            op[(int64_t)r * (N2 / IL::R) * N1] = power_of(x);
+                        }
+                    } else if (scale != 1.f) {
+                        float2 *op = static_cast<float2 *>(a.out) + o;
+#pragma unroll
+                        for (int r = 0; r < IL::R; ++r)
+                            op[(int64_t)r * (N2 / IL::R) * N1] =
+                                make_float2(v[bb * IL::R + r].x * scale, v[bb * IL::R + r].y * scale);
+                    } else {
+                        float2 *op = static_cast<float2 *>(a.out) + o;
+#pragma unroll
+                        for (int r = 0; r < IL::R; ++r) op[(int64_t)r * (N2 / IL::R) * N1] = v[bb * IL::R + r];
+                    }
+                }
             }
         }
         // P[b] (tensor-core operand staging) is refilled below
@@ -280,11 +341,9 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         if (tid == 0) {
             const int nb = b ^ 1;
             if (deferred[nb]) {  // the current tile is finished: waiting cannot deadlock
-                int isb2, c2, w2;
-                decode(item[nb], isb2, c2, w2);
                 const int *p;
                 int target;
-                dep(isb2, c2, p, target);
+                dep((int)info[4 * nb], (int)info[4 * nb + 1], p, target);
                 spin_until(p, target, a.err);
                 fence_proxy_async_global();
                 issue(item[nb], nb);

@@ -84,27 +84,72 @@ FDEV void scatter_last_b(const float2 *v, Put &&put)
 // After the last butterflies the outputs stay in v for the caller.  IN_SM:
 // this stage's inputs were read from `sm` (so a barrier must separate those
 // reads from the writes below).
+// Barrier among the T threads that run the stages: the whole CTA, or (when
+// other warps of the CTA do other work) named barrier 1 over threads 0..T-1.
+template <int T, bool NAMED>
+FDEV void stage_sync()
+{
+    if constexpr (NAMED) asm volatile("bar.sync 1, %0;" ::"n"(T) : "memory");
+    else __syncthreads();
+}
+
+// Stage twiddles of stage STAGE for this thread's butterflies, loaded ahead
+// of use (they depend only on the thread's coordinates): tw[b*(R-1) + r-1].
+template <int LOG_L, int LOG_W, bool CFAST, int T, int STAGE, bool JLAST>
+struct StageTw {
+    using I = StageInfo<LOG_L, STAGE>;
+    static constexpr int B = ((1 << (LOG_L + LOG_W)) / T) / I::R;
+    static constexpr int COUNT = I::FIRST ? 1 : B * (I::R - 1);
+    float2 w[COUNT];
+    FDEV void load(const float2 *__restrict__ twL)
+    {
+        if constexpr (!I::FIRST) {
+            constexpr int OFF = stage_table_offset<LOG_L>(STAGE);
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                int c, j;
+                stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
+                const float2 *t = twL + OFF + (j & (I::NS - 1));
+#pragma unroll
+                for (int r = 1; r < I::R; ++r) w[b * (I::R - 1) + r - 1] = __ldg(t + (r - 1) * I::NS);
+            }
+        }
+    }
+};
+
 template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true, bool JLAST = false,
-          int PREC = PREC_FP32>
-FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, const TcCtx *tc = nullptr)
+          int PREC = PREC_FP32, bool NAMED = false>
+FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, const TcCtx *tc = nullptr,
+                     const StageTw<LOG_L, LOG_W, CFAST, T, STAGE, JLAST> *pre = nullptr)
 {
     using I = StageInfo<LOG_L, STAGE>;
     constexpr int V = (1 << (LOG_L + LOG_W)) / T, B = V / I::R;
+    // the next stage's twiddles are requested now; their latency hides behind
+    // this stage's butterflies and the exchange
+    StageTw<LOG_L, LOG_W, CFAST, T, (I::LAST ? STAGE : STAGE + 1), JLAST> next;
+    if constexpr (!I::LAST) next.load(twL);
+    StageTw<LOG_L, LOG_W, CFAST, T, STAGE, JLAST> mine;
+    if constexpr (!I::FIRST) {
+        if (pre) mine = *pre;
+        else mine.load(twL);
+    }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
-        int c, j;
-        stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
+        float2 *x = v + b * I::R;
+        if constexpr (!I::FIRST) {
+#pragma unroll
+            for (int r = 1; r < I::R; ++r) x[r] = twmul<S>(x[r], mine.w[b * (I::R - 1) + r - 1]);
+        }
         if constexpr (PREC != PREC_FP32 && I::R == 16) {
             // radix-16 stages on the tensor cores (warp-collective; every
             // lane of every warp takes this branch together)
-            apply_twiddles<LOG_L, STAGE, S>(v + b * I::R, j, twL);
-            dft16_tc<S, PREC>(v + b * I::R, *tc);
+            dft16_tc<S, PREC>(x, *tc);
         } else {
-            butterfly<LOG_L, STAGE, S>(v + b * I::R, j, twL);
+            dft<I::R, S>(x);
         }
     }
     if constexpr (!I::LAST) {
-        if constexpr (IN_SM) __syncthreads();  // every thread has read this stage's inputs from sm
+        if constexpr (IN_SM) stage_sync<T, NAMED>();  // every thread has read this stage's inputs from sm
 #pragma unroll
         for (int b = 0; b < B; ++b) {
             int c, j;
@@ -114,10 +159,10 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, cons
                 sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, stockham_out_index<LOG_L, STAGE>(j, r))] =
                     v[b * I::R + r];
         }
-        __syncthreads();
+        stage_sync<T, NAMED>();
         gather<LOG_L, LOG_W, CFAST, T, STAGE + 1, JLAST>(
             v, [&](int c, int i) { return sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, i)]; });
-        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST, PREC>(v, sm, twL, tc);
+        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST, PREC, NAMED>(v, sm, twL, tc, &next);
     }
 }
 

@@ -30,6 +30,10 @@ bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_
 struct FourStepArgs;
 // prec as for launch_block (tensor-core stages for n = 2^16, 2^20, 2^24).
 cudaError_t launch_fourstep(int log_n, int sign, int prec, const FourStepArgs &a, cudaStream_t st);
+// Warp-specialised variant (FP32): producer warp + eight compute warps, TMA
+// loads and stores.
+struct FourStepWsArgs;
+cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 

@@ -9,6 +9,7 @@
 #include <cudaTypedefs.h>
 
 #include "fourstep.cuh"
+#include "fourstep_ws.cuh"
 #include "launch.h"
 #include "plan.h"
 
@@ -263,7 +264,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
 }  // namespace
 
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
-                   int64_t stride2_bytes, uint32_t box0, uint32_t box1)
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes)
 {
     const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
     const cuuint64_t strides[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
@@ -280,7 +281,8 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
             return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(base), dims, strides, box, estr,
+    CUresult r = encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
+                        const_cast<void *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -379,6 +381,45 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             return FFTSEG_OK;
         }
         case PATH_FOURSTEP: {
+            // the producer/consumer kernel stores row tiles with TMA: a box row must
+            // hold at least 16 bytes (not so for 2-point-wide power tiles at 2^24)
+            const bool ws = p->precision == FFTSEG_PREC_FP32 && (p->flags & FFTSEG_FLAG_FOURSTEP_PRODUCER) &&
+                            (int64_t(1) << p->log_wb) * (power ? 4 : 8) >= 16;
+            if (ws) {
+                FourStepWsArgs a{};
+                const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
+                const uint32_t boxa = (uint32_t)(n1 < 256 ? n1 : 256), boxb = (uint32_t)(n2 < 256 ? n2 : 256);
+                const int64_t slabs = (int64_t)p->ring_nr * p->ring_cs;
+                const int esz = power ? 4 : 8;
+                int rc = encode_tmap_3d(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, 1u << p->log_wa, boxa);
+                if (rc == FFTSEG_OK)
+                    rc = encode_tmap_3d(&a.tmB, p->ring, n1, n2, slabs, n1 * 8, n * 8, 1u << p->log_wb, boxb);
+                if (rc == FFTSEG_OK)
+                    rc = encode_tmap_3d(&a.tmY, p->ring, n1, n2, slabs, n1 * 8, n * 8, boxa, 1u << p->log_wa);
+                if (rc == FFTSEG_OK)
+                    rc = encode_tmap_3d(&a.tmO, d_out, n1, n2, nseg, n1 * esz, n * esz, 1u << p->log_wb, boxb, esz);
+                if (rc != FFTSEG_OK) return rc;
+                const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+                a.ring = p->ring;
+                a.twA = p->twA;
+                a.twB = p->twB;
+                a.w4 = p->w4;
+                a.w4hi = p->w4hi;
+                a.ctr = p->ctr;
+                a.err = p->d_err;
+                a.nseg = nseg;
+                a.nchunks = (int)nc;
+                a.cs = p->ring_cs;
+                a.nr = p->ring_nr;
+                a.out_power = power;
+                a.scale = p->scale;
+                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+                e = launch_fourstep_ws(p->log_n, sign, a, st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
+                count_launches(1);
+                return FFTSEG_OK;
+            }
             FourStepArgs a{};
             const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
             const uint32_t boxa = (uint32_t)(n1 < 256 ? n1 : 256), boxb = (uint32_t)(n2 < 256 ? n2 : 256);

@@ -55,10 +55,10 @@ int set_error(int code, const char *fmt, ...);
 int cuda_error(cudaError_t e, const char *what);
 void count_launches(int64_t k);
 
-// Tensor map over 8-byte elements: dims (d0 innermost, d1, d2), byte strides
-// of dims 1 and 2, box (box0, box1, 1).
+// Tensor map over 8-byte (or 4-byte) elements: dims (d0 innermost, d1, d2),
+// byte strides of dims 1 and 2, box (box0, box1, 1).
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
-                   int64_t stride2_bytes, uint32_t box0, uint32_t box1);
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes = 8);
 
 // Run the plan on nseg segments (arguments already validated).
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);

@@ -70,15 +70,31 @@ def test_two_pass_forced_matches_oracle(log_n, direction):
 @pytest.mark.parametrize("log_n,B", [(14, 67), (15, 33), (16, 37), (17, 9), (18, 9), (19, 5), (20, 5), (21, 3),
                                      (22, 2)])
 @pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
-def test_persistent_fourstep_matches_oracle(log_n, B, direction, norm):
-    # batches that span several chunks of the ring and end in a partial chunk
+@pytest.mark.parametrize("variant", [0, fs.FLAG_FOURSTEP_PRODUCER])
+def test_persistent_fourstep_matches_oracle(log_n, B, direction, norm, variant):
+    # batches that span several chunks of the ring and end in a partial chunk;
+    # both the all-compute kernel and the producer/consumer kernel
     n = 1 << log_n
     x = siggen.tones(800 + log_n, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2)
+    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2 | variant)
     assert plan.info()["path"] == "four-step"
     got = run(plan, x)
     assert rel_l2(got, oracle.fft(x, direction, norm)) <= tol_fp32(n)
     np.testing.assert_array_equal(run(plan, x), got)  # the dynamic schedule does not change bits
+
+
+@pytest.mark.parametrize("variant", [0, fs.FLAG_FOURSTEP_PRODUCER])
+def test_persistent_fourstep_reuses_its_ring_many_times(variant):
+    # 2^14-point segments, 128 per chunk: 1500 segments cycle the 3-chunk ring
+    # about four times, so every column tile waits on the release of a row tile
+    n, B = 1 << 14, 1500
+    x = siggen.uniform(877, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD, flags=fs.FLAG_FOURSTEP_L2 | variant)
+    assert plan.info()["work_segs"] * 3 * 3 < B
+    got = run(plan, x)
+    sample = np.r_[0:3, 700:703, B - 3:B]
+    assert rel_l2(got[sample], oracle.fft(x[sample])) <= tol_fp32(n)
+    np.testing.assert_array_equal(run(plan, x), got)
 
 
 def test_persistent_fourstep_2p24_power():
