@@ -360,6 +360,10 @@ struct ClusterArgs {
     float scale;
 };
 
+#ifndef FFTSEG_CLUSTER_MINB
+#define FFTSEG_CLUSTER_MINB 3
+#endif
+
 template <int LOG_N1, int LOG_N2, int LOG_C>
 struct ClusterShape {
     static constexpr int C = 1 << LOG_C;
@@ -375,26 +379,30 @@ struct ClusterShape {
     static constexpr int Q = 1 << (LOG_WA + LOG_WB);
     static constexpr int SLICE = Q + (Q >> PSB);
     static constexpr int SEND = C * SLICE;
-    static constexpr int SLOTS_S = ((SLOTS_A > SEND ? SLOTS_A : SEND) + 1) & ~1;
+    static constexpr int U0 = SLOTS_A > SEND ? SLOTS_A : SEND;
+    static constexpr int SLOTS_U = ((U0 > E ? U0 : E) + 1) & ~1;
     static constexpr int SLOTS_X = (SLOTS_B + 1) & ~1;
     static constexpr int R_LAST = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>::R;
-    // P (prefetch tile) | S (column-pass scratch, then send staging) | X (row pass) | TR | barriers
+    // U (input tile, column-pass scratch, send staging) | X (row pass) | TR | barriers
     static constexpr size_t SMEM =
-        (size_t)(E + SLOTS_S + SLOTS_X + R_LAST * (1 << LOG_WA)) * sizeof(float2) + 2 * sizeof(uint64_t);
-    static constexpr int MINB = T <= 256 ? 2 : 1;  // CTAs per SM the register budget must allow
+        (size_t)(SLOTS_U + SLOTS_X + R_LAST * (1 << LOG_WA)) * sizeof(float2) + 2 * sizeof(uint64_t);
+    static constexpr int MINB = T <= 256 ? FFTSEG_CLUSTER_MINB : 1;  // CTAs per SM the registers must allow
 };
 
 // One cluster of C CTAs per segment, persistent over segments
 // s = cluster, cluster + nclusters, ...  CTA r of the cluster owns the column
 // slab j2 in [r*WA, (r+1)*WA) (N1 rows of WA points) in the column pass and
-// the rows k1 in [r*WB, (r+1)*WB) in the row pass.
-//  - The slab of the next segment arrives by one tiled TMA copy, issued as
-//    soon as the current slab has been read into registers.
-//  - The column-pass results, times the four-step twiddle, are laid out in S
-//    exactly as each receiver's row-pass buffer X wants them (one slice per
-//    receiver) and go out as C bulk shared-to-shared copies that complete on
-//    the receiver's barrier `rbar`; a relaxed cluster barrier first makes sure
-//    no receiver still reads its X.
+// the rows k1 in [r*WB, (r+1)*WB) in the row pass.  Two shared buffers:
+//  - U receives the slab (one tiled TMA copy), serves as the column pass's
+//    exchange buffer, and finally stages the column-pass results times the
+//    four-step twiddle exactly as each receiver's row-pass buffer wants them
+//    (one slice per receiver); C bulk shared-to-shared copies send the slices,
+//    completing on the receivers' barriers `rbar`.  Once those copies have
+//    read U, the next segment's slab is requested into it, so the load
+//    overlaps the row pass.
+//  - X receives the slices and serves as the row pass's exchange buffer; a
+//    relaxed cluster barrier makes sure no receiver still reads it before the
+//    copies are sent.
 //  - Four-step twiddle w_n^{j2 k1} with k1 = j + (N1/R)*q (j = butterfly
 //    index of the last column stage): w_n^{j2 j} (per thread, kept in
 //    registers) times w_n^{j2 (N1/R) q} (table TR in shared memory), both
@@ -408,19 +416,17 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
     constexpr int64_t N = (int64_t)N1 * N2;
     constexpr int LOG_STEP = LOG_N1 - StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>::LOG_R;  // log2(N1/R)
-    // tiled TMA writes need a 128-byte aligned destination: the prefetch
-    // tile comes first (base 1024-byte aligned, a multiple of 1024 bytes)
+    // the tiled TMA write needs a 128-byte aligned destination: U comes first
     extern __shared__ __align__(1024) float2 sm[];
-    float2 *P = sm;
-    float2 *Sb = P + E;
-    float2 *X = Sb + Sh::SLOTS_S;
+    float2 *U = sm;
+    float2 *X = U + Sh::SLOTS_U;
     float2 *TR = X + Sh::SLOTS_X;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(TR + Sh::R_LAST * WA);  // TMA tile arrived
+    uint64_t *bar = reinterpret_cast<uint64_t *>(TR + Sh::R_LAST * WA);  // slab arrived
     uint64_t *rbar = bar + 1;                                            // row-pass slices arrived
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
     const int tid = threadIdx.x;
-    if (smem_u32(P) & 127) {  // same layout in every CTA: the whole cluster leaves together
+    if (smem_u32(U) & 127) {  // same layout in every CTA: the whole cluster leaves together
         if (tid == 0) atomicOr(a.err, 2);
         return;
     }
@@ -445,51 +451,50 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
     cl.sync();  // every peer's barriers are initialised before any copy reaches them
     const uint32_t x_remote0 = smem_u32(X) + (uint32_t)(rank * Sh::SLICE * sizeof(float2));
 
-    auto issue = [&](int64_t s) {
-        if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect_tx(&bar[0], (uint32_t)(E * sizeof(float2)));
-            tma_load_3d(P, &a.tmap, rank * WA, 0, (int)s, &bar[0]);
-        }
+    auto issue = [&](int64_t s) {  // thread 0
+        fence_proxy_async();
+        mbar_expect_tx(bar, (uint32_t)(E * sizeof(float2)));
+        tma_load_3d(U, &a.tmap, rank * WA, 0, (int)s, bar);
     };
 
     const int64_t cid = blockIdx.x >> LOG_C, ncl = gridDim.x >> LOG_C;
     int64_t s = cid;
-    if (s < a.nseg) issue(s);
+    if (s < a.nseg && tid == 0) issue(s);
     const float scale = a.scale;
     for (int k = 0; s < a.nseg; s += ncl, ++k) {
-        if (tid == 0) {
-            mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
-            bulk_wait_read_all();  // the previous segment's outgoing copies no longer read S
-        }
-        mbar_wait(&bar[0], k & 1, a.err);
+        if (tid == 0) mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
+        mbar_wait(bar, k & 1, a.err);
         float2 v[16];
 
         // column pass: line c is column j2 = rank*WA + c, points j1 = i
-        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return P[i * WA + c]; });
-        __syncthreads();  // P fully read (refill it) and S free
-        if (s + ncl < a.nseg) issue(s + ncl);
-        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, false>(v, Sb, a.twA);
-        __syncthreads();  // S no longer read as column-pass scratch
+        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return U[i * WA + c]; });
+        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, true>(v, U, a.twA);
+        __syncthreads();  // U no longer read as column-pass scratch
 
-        // send staging: slice d of S holds, for receiver d, element
+        // send staging: slice d of U holds, for receiver d, element
         // (k1, j2) at q' = (j2 - rank*WA)*WB + (k1 mod WB), padded as in X
         scatter_last_b<LOG_N1, Sh::LOG_WA, true, T>(v, [&](int b, int c, int k1, float2 x) {
             const float2 w = TR[(k1 >> LOG_STEP) * WA + c];  // k1 = j + (N1/R) q
             const float2 wb = wbase[b];
             x = twmul<S>(x, make_float2(w.x * wb.x - w.y * wb.y, w.x * wb.y + w.y * wb.x));
             const int qq = c * WB + (k1 & (WB - 1));
-            Sb[(k1 >> Sh::LOG_WB) * Sh::SLICE + qq + (qq >> Sh::PSB)] = x;
+            U[(k1 >> Sh::LOG_WB) * Sh::SLICE + qq + (qq >> Sh::PSB)] = x;
         });
         fence_proxy_async();      // these generic writes are read by the async-proxy copies below
-        __syncthreads();          // S complete
+        __syncthreads();          // U complete
         cluster_sync_relaxed();   // no receiver still reads its X
-        if (tid < C) {
-            dsmem_bulk_copy(mapa_u32(x_remote0, tid), Sb + tid * Sh::SLICE, Sh::SLICE * sizeof(float2),
-                            mapa_u32(smem_u32(rbar), tid));
+        if (tid == 0) {
+#pragma unroll 1
+            for (int d = 0; d < C; ++d)
+                dsmem_bulk_copy(mapa_u32(x_remote0, d), U + d * Sh::SLICE, Sh::SLICE * sizeof(float2),
+                                mapa_u32(smem_u32(rbar), d));
             bulk_commit();
         }
         mbar_wait(rbar, k & 1, a.err);  // every slice of this CTA's rows has arrived
+        if (tid == 0) {
+            bulk_wait_read_all();  // the outgoing copies have read U: refill it
+            if (s + ncl < a.nseg) issue(s + ncl);
+        }
 
         // row pass: line c is row k1 = rank*WB + c, points j2 = i
         gather<LOG_N2, Sh::LOG_WB, true, T, 0>(
@@ -504,7 +509,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             else static_cast<float2 *>(a.out)[o] = x;
         });
     }
-    if (tid < C) bulk_wait_read_all();
+    if (tid == 0) bulk_wait_read_all();
     cl.sync();  // no CTA leaves while a peer could still copy into its X
 }
 
