@@ -35,6 +35,13 @@ UNIT = "GFLOP/s"
 WORKLOAD = "resident 8 GiB complex64 signal, 16384 segments x 65536 points, forward then inverse (1/n)"
 
 
+def workload_name(segments):
+    if segments == SEGMENTS:
+        return WORKLOAD
+    return ("resident %g GiB complex64 signal, %d segments x %d points, forward then inverse (1/n)"
+            % (segments * N * 8 / 2**30, segments, N))
+
+
 def flops_per_transform(n, segments):
     return 5.0 * n * math.log2(n) * segments
 
@@ -336,20 +343,21 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
+    S = args.segments
 
     # ---- inputs: synthesised on the host straight into pinned memory
-    h_in = torch.empty(SEGMENTS * N, dtype=torch.complex64, pin_memory=True)
-    siggen.fill_pointer(siggen.KIND_TONES, SEED, 0, SEGMENTS * N, h_in.data_ptr())
-    h_out = torch.empty(SEGMENTS * N, dtype=torch.complex64, pin_memory=True)
-    x = h_in.to(dev).view(SEGMENTS, N)
+    h_in = torch.empty(S * N, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_TONES, SEED, 0, S * N, h_in.data_ptr())
+    h_out = torch.empty(S * N, dtype=torch.complex64, pin_memory=True)
+    x = h_in.to(dev).view(S, N)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
-    fwd = fs.Plan(N, SEGMENTS, fs.FORWARD, fs.NORM_NONE)
-    inv = fs.Plan(N, SEGMENTS, fs.INVERSE, fs.NORM_BACKWARD)
+    fwd = fs.Plan(N, S, fs.FORWARD, fs.NORM_NONE)
+    inv = fs.Plan(N, S, fs.INVERSE, fs.NORM_BACKWARD)
 
     def step():
-        fwd.exec_ptr(x.data_ptr(), y.data_ptr(), SEGMENTS, stream)
-        inv.exec_ptr(y.data_ptr(), z.data_ptr(), SEGMENTS, stream)
+        fwd.exec_ptr(x.data_ptr(), y.data_ptr(), S, stream)
+        inv.exec_ptr(y.data_ptr(), z.data_ptr(), S, stream)
 
     def barrier():
         torch.cuda.synchronize()
@@ -375,9 +383,9 @@ def run_ours(args):
         for i in range(args.steps):
             a, b, c = evs[i]
             a.record(stream)
-            fwd.exec_ptr(x.data_ptr(), y.data_ptr(), SEGMENTS, stream)
+            fwd.exec_ptr(x.data_ptr(), y.data_ptr(), S, stream)
             b.record(stream)
-            inv.exec_ptr(y.data_ptr(), z.data_ptr(), SEGMENTS, stream)
+            inv.exec_ptr(y.data_ptr(), z.data_ptr(), S, stream)
             c.record(stream)
         e_end.record(stream)
         barrier()
@@ -390,7 +398,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     ms_per_step = ms / args.steps
-    flops_step = 2 * flops_per_transform(N, SEGMENTS)
+    flops_step = 2 * flops_per_transform(N, S)
     value = world * flops_step / (ms_per_step / 1e3) / 1e9
 
     # round-trip check of this very run (inverse(forward(x)) == x up to rounding)
@@ -399,7 +407,7 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
     per_launch_ms = statistics.mean(kernel_ms)
-    algo_bytes = 16.0 * N * SEGMENTS
+    algo_bytes = 16.0 * N * S
     achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
     traffic = measured_traffic("%s:%d" % (fwd.info()["path"], N))
 
@@ -420,9 +428,9 @@ def run_ours(args):
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": N, "segments": SEGMENTS, "path": fwd.info()["path"],
+                "config": {"workload": workload_name(S), "n": N, "segments": S, "path": fwd.info()["path"],
                            "signal": "32 off-bin tones (log-uniform 1e-3..1) + complex Gaussian noise sigma 0.1, seed 1",
-                           "l2": "inputs larger than L2 (8 GiB per buffer), no flush needed",
+                           "l2": "inputs larger than L2 (%g GiB per buffer), no flush needed" % (S * N * 8 / 2**30),
                            "replicas": "one independent replica per GPU (no collective on the data path)"},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "traffic": traffic,
@@ -459,6 +467,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the tensor-core split and the serving run")
+    ap.add_argument("--segments", type=int, default=SEGMENTS,
+                    help="segments per transform (default 16384; smaller only for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
