@@ -200,7 +200,7 @@ __host__ __device__ constexpr int stage_table_offset(int stage)
 }
 
 // Twiddle + DFT of one butterfly held in x[0..R).  tw: the stage tables of
-// a length-L line (see StageTable).
+// a length-L line (laid out as stage_table_offset gives).
 template <int LOG_L, int STAGE, int S>
 FDEV void apply_twiddles(float2 *x, int j, const float2 *__restrict__ tw)
 {
@@ -355,6 +355,10 @@ FDEV void cluster_sync_relaxed()
 {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
+
+// The two halves of cluster_sync_relaxed, for an arrive early and a wait late.
+FDEV void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+FDEV void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;" ::: "memory"); }
 
 FDEV bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 {

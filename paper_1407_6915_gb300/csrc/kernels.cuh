@@ -101,6 +101,8 @@ struct StageTw {
     static constexpr int B = ((1 << (LOG_L + LOG_W)) / T) / I::R;
     static constexpr int COUNT = I::FIRST ? 1 : B * (I::R - 1);
     float2 w[COUNT];
+    // TW_SM: twL points into shared memory (plain loads), else global (read-only path)
+    template <bool TW_SM = false>
     FDEV void load(const float2 *__restrict__ twL)
     {
         if constexpr (!I::FIRST) {
@@ -111,27 +113,31 @@ struct StageTw {
                 stage_coords<LOG_L, LOG_W, CFAST, JLAST, STAGE>(threadIdx.x + T * b, c, j);
                 const float2 *t = twL + OFF + (j & (I::NS - 1));
 #pragma unroll
-                for (int r = 1; r < I::R; ++r) w[b * (I::R - 1) + r - 1] = __ldg(t + (r - 1) * I::NS);
+                for (int r = 1; r < I::R; ++r) {
+                    if constexpr (TW_SM) w[b * (I::R - 1) + r - 1] = t[(r - 1) * I::NS];
+                    else w[b * (I::R - 1) + r - 1] = __ldg(t + (r - 1) * I::NS);
+                }
             }
         }
     }
 };
 
 template <int LOG_L, int LOG_W, bool CFAST, int S, int T, int PS, int STAGE, bool IN_SM = true, bool JLAST = false,
-          int PREC = PREC_FP32, bool NAMED = false>
+          int PREC = PREC_FP32, bool NAMED = false, bool TW_SM = false>
 FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, const TcCtx *tc = nullptr,
                      const StageTw<LOG_L, LOG_W, CFAST, T, STAGE, JLAST> *pre = nullptr)
 {
     using I = StageInfo<LOG_L, STAGE>;
     constexpr int V = (1 << (LOG_L + LOG_W)) / T, B = V / I::R;
-    // the next stage's twiddles are requested now; their latency hides behind
-    // this stage's butterflies and the exchange
+    // the next stage's twiddles are requested now (global tables); their
+    // latency hides behind this stage's butterflies and the exchange.  Tables
+    // in shared memory are read at use.
     StageTw<LOG_L, LOG_W, CFAST, T, (I::LAST ? STAGE : STAGE + 1), JLAST> next;
-    if constexpr (!I::LAST) next.load(twL);
+    if constexpr (!I::LAST && !TW_SM) next.load(twL);
     StageTw<LOG_L, LOG_W, CFAST, T, STAGE, JLAST> mine;
     if constexpr (!I::FIRST) {
         if (pre) mine = *pre;
-        else mine.load(twL);
+        else mine.template load<TW_SM>(twL);
     }
 #pragma unroll
     for (int b = 0; b < B; ++b) {
@@ -162,7 +168,8 @@ FDEV void run_stages(float2 *v, float2 *sm, const float2 *__restrict__ twL, cons
         stage_sync<T, NAMED>();
         gather<LOG_L, LOG_W, CFAST, T, STAGE + 1, JLAST>(
             v, [&](int c, int i) { return sm[smem_slot<LOG_L, LOG_W, CFAST, PS>(c, i)]; });
-        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST, PREC, NAMED>(v, sm, twL, tc, &next);
+        run_stages<LOG_L, LOG_W, CFAST, S, T, PS, STAGE + 1, true, JLAST, PREC, NAMED, TW_SM>(v, sm, twL, tc,
+                                                                                          TW_SM ? nullptr : &next);
     }
 }
 
@@ -383,9 +390,12 @@ struct ClusterShape {
     static constexpr int SLOTS_U = ((U0 > E ? U0 : E) + 1) & ~1;
     static constexpr int SLOTS_X = (SLOTS_B + 1) & ~1;
     static constexpr int R_LAST = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>::R;
-    // U (input tile, column-pass scratch, send staging) | X (row pass) | TR | barriers
+    // stage twiddle tables of the column and row lines (one copy when N1 == N2)
+    static constexpr int TWA = stage_table_offset<LOG_N1>(StageInfo<LOG_N1, 0>::NSTAGES);
+    static constexpr int TWB = LOG_N1 == LOG_N2 ? 0 : stage_table_offset<LOG_N2>(StageInfo<LOG_N2, 0>::NSTAGES);
+    // U (input tile, column-pass scratch, send staging) | X (row pass) | TR | stage tables | barriers
     static constexpr size_t SMEM =
-        (size_t)(SLOTS_U + SLOTS_X + R_LAST * (1 << LOG_WA)) * sizeof(float2) + 2 * sizeof(uint64_t);
+        (size_t)(SLOTS_U + SLOTS_X + R_LAST * (1 << LOG_WA) + TWA + TWB) * sizeof(float2) + 2 * sizeof(uint64_t);
     static constexpr int MINB = T <= 256 ? FFTSEG_CLUSTER_MINB : 1;  // CTAs per SM the registers must allow
 };
 
@@ -400,9 +410,12 @@ struct ClusterShape {
 //    completing on the receivers' barriers `rbar`.  Once those copies have
 //    read U, the next segment's slab is requested into it, so the load
 //    overlaps the row pass.
-//  - X receives the slices and serves as the row pass's exchange buffer; a
+//  - X receives the slices and serves as the row pass's exchange buffer.  A
 //    relaxed cluster barrier makes sure no receiver still reads it before the
-//    copies are sent.
+//    copies are sent: each CTA arrives once its row pass has consumed X (end
+//    of an iteration) and waits just before it sends (after the next column
+//    pass), so the barrier's latency hides behind a column pass.
+//  - The stage twiddle tables are copied into shared memory once.
 //  - Four-step twiddle w_n^{j2 k1} with k1 = j + (N1/R)*q (j = butterfly
 //    index of the last column stage): w_n^{j2 j} (per thread, kept in
 //    registers) times w_n^{j2 (N1/R) q} (table TR in shared memory), both
@@ -421,7 +434,9 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
     float2 *U = sm;
     float2 *X = U + Sh::SLOTS_U;
     float2 *TR = X + Sh::SLOTS_X;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(TR + Sh::R_LAST * WA);  // slab arrived
+    float2 *TWA = TR + Sh::R_LAST * WA;
+    float2 *TWB = LOG_N1 == LOG_N2 ? TWA : TWA + Sh::TWA;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(TWA + Sh::TWA + Sh::TWB);  // slab arrived
     uint64_t *rbar = bar + 1;                                            // row-pass slices arrived
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -437,6 +452,9 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
     }
     for (int e = tid; e < Sh::R_LAST * WA; e += T)  // TR[q][c] = w_n^{(rank*WA + c) (N1/R) q}
         TR[e] = __ldg(a.tw4 + (int64_t)((e >> Sh::LOG_WA) << LOG_STEP) * N2 + rank * WA + (e & (WA - 1)));
+    for (int e = tid; e < Sh::TWA; e += T) TWA[e] = __ldg(a.twA + e);
+    if constexpr (Sh::TWB > 0)
+        for (int e = tid; e < Sh::TWB; e += T) TWB[e] = __ldg(a.twB + e);
     // w_n^{j2 j} for this thread's butterflies of the last column stage
     float2 wbase[(E / T) / Sh::R_LAST];
     {
@@ -461,6 +479,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
     int64_t s = cid;
     if (s < a.nseg && tid == 0) issue(s);
     const float scale = a.scale;
+    cluster_arrive_relaxed();  // X is free
     for (int k = 0; s < a.nseg; s += ncl, ++k) {
         if (tid == 0) mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
         mbar_wait(bar, k & 1, a.err);
@@ -468,7 +487,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
 
         // column pass: line c is column j2 = rank*WA + c, points j1 = i
         gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return U[i * WA + c]; });
-        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, true>(v, U, a.twA);
+        run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, true, false, PREC_FP32, false, true>(v, U, TWA);
         __syncthreads();  // U no longer read as column-pass scratch
 
         // send staging: slice d of U holds, for receiver d, element
@@ -482,7 +501,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
         });
         fence_proxy_async();      // these generic writes are read by the async-proxy copies below
         __syncthreads();          // U complete
-        cluster_sync_relaxed();   // no receiver still reads its X
+        cluster_wait();           // no receiver still reads its X
         if (tid == 0) {
 #pragma unroll 1
             for (int d = 0; d < C; ++d)
@@ -499,7 +518,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
         // row pass: line c is row k1 = rank*WB + c, points j2 = i
         gather<LOG_N2, Sh::LOG_WB, true, T, 0>(
             v, [&](int c, int i) { return X[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(c, i)]; });
-        run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0>(v, X, a.twB);
+        run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0, true, false, PREC_FP32, false, true>(v, X, TWB);
 
         const int64_t obase = s * N + rank * WB;
         scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
@@ -508,7 +527,9 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
             else static_cast<float2 *>(a.out)[o] = x;
         });
+        cluster_arrive_relaxed();  // this thread's reads of X were consumed above
     }
+    cluster_wait();
     if (tid == 0) bulk_wait_read_all();
     cl.sync();  // no CTA leaves while a peer could still copy into its X
 }
