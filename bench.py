@@ -157,6 +157,95 @@ def measured_traffic(key):
     return None
 
 
+def link_peaks(dev, gib=1, reps=3):
+    """Measured pinned host<->device copy rates (GB/s): each direction alone
+    and both at once on two streams (each way), best of `reps`."""
+    import torch
+    n = gib << 27
+    h1 = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+    h2 = torch.empty(n, dtype=torch.complex64, pin_memory=True)
+    h1.zero_()
+    d1 = torch.empty(n, dtype=torch.complex64, device=dev)
+    d2 = torch.zeros(n, dtype=torch.complex64, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    nb = n * 8
+    best = {"h2d": 0.0, "d2h": 0.0, "concurrent_each_way": 0.0}
+    for _ in range(reps):
+        for key, fn in (("h2d", lambda: d1.copy_(h1, non_blocking=True)),
+                        ("d2h", lambda: h2.copy_(d2, non_blocking=True))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            best[key] = max(best[key], nb / (time.perf_counter() - t0) / 1e9)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            d1.copy_(h1, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+        torch.cuda.synchronize()
+        best["concurrent_each_way"] = max(best["concurrent_each_way"], nb / (time.perf_counter() - t0) / 1e9)
+    del h1, h2, d1, d2
+    return {k: round(v, 1) for k, v in best.items()}
+
+
+def stream_bench(link, h_signal=None):
+    """The out-of-core stream on a bounded sample: the tones + noise signal
+    (seed 2) generated on the host as it is read, through fftseg_stream in
+    2^20-point segments with |X|^2 output, chunks of 64 segments; then a
+    host-resident batch of the same shape through fftseg_exec_host, which
+    leaves out the generator and shows the pipeline against the link."""
+    import ctypes
+    import torch
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    n = 1 << 20
+    chunk = 64
+    nseg = 1024  # 8 GiB of the 128 GiB signal
+    total = nseg * n * 8
+    flops = flops_per_transform(n, nseg)
+    plan = fs.Plan(n, chunk, fs.FORWARD, out_kind=fs.OUT_POWER)
+    src = siggen.source(siggen.KIND_TONES, 2, total)
+    snk = siggen.sink(None)  # counts the bytes, keeps nothing
+    t0 = time.perf_counter()
+    rc, committed = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(src), siggen.write_fn_ptr(),
+                                ctypes.addressof(snk), total, 0, chunk)
+    wall = time.perf_counter() - t0
+    ph = plan.stream_phases()
+    h2d_gbs, d2h_gbs = total / wall / 1e9, total / 2 / wall / 1e9
+    gen_gbs = total / (ph["read_ms"] / 1e3) / 1e9 if ph["read_ms"] > 0 else None
+    out = {"n": n, "segments": nseg, "chunk_segments": chunk, "input_bytes": total, "status": rc,
+           "output_bytes": int(snk.bytes_written), "wall_s": round(wall, 3),
+           "gflops": round(flops / wall / 1e9, 1),
+           "h2d_gbs": round(h2d_gbs, 2), "d2h_gbs": round(d2h_gbs, 2),
+           "link_frac": round(max(h2d_gbs / link["h2d"], d2h_gbs / link["d2h"]), 4),
+           "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+           "generator_gbs": round(gen_gbs, 2) if gen_gbs else None,
+           "generator_threads": int(src.nthreads),
+           "bound": "generator" if ph["read_ms"] > 0.8 * ph["wall_ms"] else "pipeline",
+           "full_128gib_s_extrapolated": round(wall * 16, 1)}
+    plan.destroy()
+    if h_signal is not None:
+        hn = min(h_signal.numel() // n, 512)
+        hp = fs.Plan(n, chunk, fs.FORWARD, out_kind=fs.OUT_POWER)
+        h_pow = torch.empty(hn * n, dtype=torch.float32, pin_memory=True)
+        for _ in range(3):  # staging, first touch, link ramp-up
+            fs.exec_host([hp], h_signal.data_ptr(), h_pow.data_ptr(), hn, chunk)
+        t0 = time.perf_counter()
+        fs.exec_host([hp], h_signal.data_ptr(), h_pow.data_ptr(), hn, chunk)
+        dt = time.perf_counter() - t0
+        in_gbs = hn * n * 8 / dt / 1e9
+        out["host_resident"] = {"call": "fftseg_exec_host, |X|^2 out", "segments": hn,
+                                "input_bytes": hn * n * 8, "s": round(dt, 4),
+                                "gflops": round(flops_per_transform(n, hn) / dt / 1e9, 1),
+                                "h2d_gbs": round(in_gbs, 1), "d2h_gbs": round(in_gbs / 2, 1),
+                                "link_frac": round(max(in_gbs / link["h2d"], in_gbs / 2 / link["d2h"]), 4)}
+        hp.destroy()
+        del h_pow
+    return out
+
+
 def tc_split(peak):
     """FP32 versus tensor-core (split hi+lo FP16 / BF16) on the same GPU: time of one
     4 GiB batch and relative L2 error against the FP64 oracle on a sample of segments."""
@@ -411,17 +500,27 @@ def run_ours(args):
     achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
     traffic = measured_traffic("%s:%d" % (fwd.info()["path"], N))
 
-    # ---- end to end through the public API with host buffers
-    e2e_steps = max(1, min(args.steps, 3))
+    # ---- end to end through the public API with host buffers: fftseg_exec_host
+    # runs the forward + inverse chain over the pinned host signal in chunks,
+    # copies in both directions overlapped with the transforms
+    # (untimed warm-up calls: the first host transfers after an idle spell run
+    # several times slower while the host link ramps up)
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(args.warmup):
+        fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)
     barrier()
     t0 = time.perf_counter()
+    e2e_step_ms = []
     for _ in range(e2e_steps):
-        x.view(-1).copy_(h_in, non_blocking=True)
-        step()
-        h_out.copy_(z.view(-1), non_blocking=True)
+        t1 = time.perf_counter()
+        fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)  # synchronous
+        e2e_step_ms.append(round((time.perf_counter() - t1) * 1e3, 2))
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     e2e_value = world * flops_step / e2e_s / 1e9
+    link = link_peaks(dev)
+    k = min(S, 4)
+    e2e_err = float(torch.linalg.vector_norm((h_out[: k * N] - h_in[: k * N])) / torch.linalg.vector_norm(h_in[: k * N]))
 
     line = None
     if rank == 0:
@@ -439,7 +538,12 @@ def run_ours(args):
                              "algorithmic_bytes_per_launch": algo_bytes,
                              "mean_launch_ms": round(per_launch_ms, 4)},
                 "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
-                        "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2)},
+                        "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2),
+                        "step_ms": e2e_step_ms, "warmup_calls": args.warmup, "call": "fftseg_exec_host([forward, inverse]) on pinned host buffers",
+                        "link_gbs_each_way": round(x.numel() * 8 / e2e_s / 1e9, 1),
+                        "link_peaks_gbs": link,
+                        "link_frac": round(x.numel() * 8 / e2e_s / 1e9 / link["concurrent_each_way"], 4),
+                        "round_trip_rel_l2_first_%d_segments" % k: e2e_err},
                 "gpu_launches": int(launches),
                 "clocks": clk.summary(),
                 "round_trip_rel_l2": err}
@@ -448,6 +552,7 @@ def run_ours(args):
         if world == 1 and not args.no_extras:
             del x, y, z
             torch.cuda.empty_cache()
+            line["stream"] = stream_bench(link, h_in)
             line["tc_split"] = tc_split(peak)
             line["serve"] = serve_bench(peak)
     if world > 1:

@@ -134,6 +134,30 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
  * out[4] write callback, out[5] wall time. */
 int fftseg_stream_phases(fftseg_plan p, double out[6]);
 
+/*
+ * A batch held in host memory through a chain of plans (Sec. III's copy in,
+ * transform, copy back, as one overlapped pipeline): h_in [nseg][n] complex64
+ * -> plans[0] -> plans[1] -> ... -> plans[nplans-1] -> h_out [nseg][n]
+ * (complex64, or float32 when the last plan writes the power output).
+ *   plans          nplans >= 1 plans of the same n on the current device;
+ *                  all but the last must write complex output.
+ *   h_in, h_out    host memory the caller owns (pinned runs at full link
+ *                  speed; pageable works where the driver can stage it).
+ *                  h_in == h_out transforms in place; other overlaps are
+ *                  undefined.
+ *   chunk_segments segments per chunk, 1..the smallest plan batch; 0 picks
+ *                  about 256 MiB of input per chunk.
+ * Chunk c+1 is copied to the device while chunk c runs through the plans and
+ * chunk c-1 is copied back, on three streams the library owns.  The device
+ * staging (three slots of two chunk buffers) is allocated on first use and
+ * kept with plans[0] until fftseg_plan_destroy.  Synchronous: h_out is
+ * complete when the call returns FFTSEG_OK.  A failing CUDA call returns
+ * FFTSEG_E_CUDA (or E_NOMEM for the staging); the content of h_out is then
+ * undefined.
+ */
+int fftseg_exec_host(const fftseg_plan *plans, int nplans, const void *h_in, void *h_out, int64_t nseg,
+                     int64_t chunk_segments);
+
 int fftseg_plan_destroy(fftseg_plan p);
 
 /* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core,

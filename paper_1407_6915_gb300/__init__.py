@@ -69,6 +69,10 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "fftseg_exec_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "fftseg_exec_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "fftseg_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fftseg_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_plan_check": (ctypes.c_int, [ctypes.c_void_p]),
@@ -125,6 +129,15 @@ def _ptr(t):
     return t if isinstance(t, int) else t.data_ptr()
 
 
+def exec_host(plans, h_in, h_out, nseg, chunk_segments=0) -> None:
+    """fftseg_exec_host: nseg segments in host memory (tensors or addresses)
+    through the plans in order; synchronous."""
+    plans = list(plans) if isinstance(plans, (list, tuple)) else [plans]
+    arr = (ctypes.c_void_p * len(plans))(*[p.handle for p in plans])
+    check(lib().fftseg_exec_host(arr, len(plans), _ptr(h_in), _ptr(h_out), int(nseg), int(chunk_segments)),
+          "fftseg_exec_host")
+
+
 def segment_offset(s: int, n: int, sample_bytes: int = 8) -> int:
     """Byte offset of segment s (Sec. III: offset = bytes from the start of the file)."""
     return s * n * sample_bytes
@@ -161,6 +174,10 @@ class Plan:
         """Raw-pointer form of fftseg_exec_n (asynchronous on `stream`)."""
         nseg = self.batch if nseg is None else nseg
         check(lib().fftseg_exec_n(self._h, d_in, d_out, nseg, _stream_handle(stream)), "fftseg_exec")
+
+    def exec_host(self, h_in, h_out, nseg=None, chunk_segments=0) -> None:
+        """fftseg_exec_host with this plan alone (host tensors or addresses)."""
+        exec_host([self], h_in, h_out, self.batch if nseg is None else nseg, chunk_segments)
 
     def exec(self, x, out=None, nseg=None, stream=None):
         """Transform the first nseg segments of the device tensor x (complex64,

@@ -118,6 +118,7 @@ int fourstep_table(float2 **dst, int64_t n, int64_t rows, int64_t row_mult, int6
 void free_plan(fftseg_plan p)
 {
     if (!p) return;
+    if (p->host_stage && p->host_stage_free) p->host_stage_free(p->host_stage);
     cudaFree(p->twA);
     cudaFree(p->twB);
     cudaFree(p->tw4a);

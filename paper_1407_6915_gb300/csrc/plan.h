@@ -46,6 +46,9 @@ struct fftseg_plan_s {
     int log_wa = 0, log_wb = 0;
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
+    // fftseg_exec_host device staging (owned; released with the plan)
+    void *host_stage = nullptr;
+    void (*host_stage_free)(void *) = nullptr;
 };
 
 namespace fftseg {
