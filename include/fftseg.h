@@ -188,7 +188,7 @@ int64_t fftseg_launch_count(void);
  *   - real-time processing threads, where cudaMalloc may synchronise the device
  *     and take an unbounded time.
  * This entry point needs no plan and calls no cudaMalloc, cudaFree or other
- * allocating routine. Its scratch is one fixed array of about 32.5 MiB,
+ * allocating routine. Its scratch is one fixed array of about 25.5 MiB,
  * compiled into the library, which every GPU that loads the library holds
  * until the process exits. The scratch holds:
  *   - the L2 ring of three 8 MiB chunks;

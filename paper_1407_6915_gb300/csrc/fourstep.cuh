@@ -18,8 +18,14 @@
 // Each CTA double-buffers its input tiles: the next tile's TMA copy is issued
 // while the current tile is transformed whenever the next tile's dependency is
 // already met.
+//
+// Shared memory also holds the stage twiddle tables (lines up to 2048
+// points) and, per A tile, the two factor tables of the four-step twiddle for
+// the tile's columns, so that the only global loads of a tile are its TMA
+// copy and those few table entries.
 #pragma once
 #include "kernels.cuh"
+#include "launch.h"
 
 namespace fftseg {
 
@@ -30,8 +36,8 @@ struct FourStepArgs {
     float2 *ring;           // NR*CS segments of n points, [slot*CS + sl][j2][k1]
     const float2 *twA;      // stage tables, length N1
     const float2 *twB;      // stage tables, length N2
-    const float2 *w4;       // [j2][k1 mod K] = w_n^{j2 (k1 mod K)}, K = 64 above 2^20, else N1
-    const float2 *w4hi;     // [j2][k1 >> 6] = w_n^{j2 64 (k1 >> 6)} above 2^20, else unused
+    const float2 *w4;       // [j2][k1 mod K] = w_n^{j2 (k1 mod K)}, K = 2^fourstep_log_k(log2 N1)
+    const float2 *w4hi;     // [j2][k1 div K] = w_n^{j2 K (k1 div K)}
     int *ctr;               // [0] queue head, [1 + c] A tiles done, [1 + NC + c] B tiles done
     int *err;
     int64_t nseg;
@@ -55,8 +61,19 @@ struct FourStepShape {
     static constexpr int SLOTS_A = smem_slots<LOG_N1, LOG_WA, PS>();
     static constexpr int SLOTS_B = smem_slots<LOG_N2, LOG_WB, PS>();
     static constexpr int SLOTS = ((SLOTS_A > SLOTS_B ? SLOTS_A : SLOTS_B) + 1) & ~1;
-    // P[2] (input tiles) | X (stage scratch) | 2 barriers | 2 item slots
-    static constexpr size_t SMEM = (size_t)(2 * E + SLOTS) * sizeof(float2) + 2 * sizeof(uint64_t) + 10 * sizeof(int64_t);
+    // stage twiddle tables in shared memory for lines up to 2048 points (one
+    // copy when N1 == N2); longer lines read them from global memory
+    static constexpr bool TW_SM = LOG_N1 <= 11 && LOG_N2 <= 11;
+    static constexpr int TWA = TW_SM ? stage_table_offset<LOG_N1>(StageInfo<LOG_N1, 0>::NSTAGES) : 0;
+    static constexpr int TWB =
+        TW_SM && LOG_N1 != LOG_N2 ? stage_table_offset<LOG_N2>(StageInfo<LOG_N2, 0>::NSTAGES) : 0;
+    // four-step twiddle factors of an A tile's columns: per column K + N1/K entries
+    static constexpr int LOG_K = fourstep_log_k(LOG_N1);
+    static constexpr int FK = (1 << LOG_K) + (N1 >> LOG_K);
+    static constexpr int FA = FK << LOG_WA;
+    // P[2] (input tiles) | X (stage scratch) | stage tables | factors | 2 barriers | 2 item slots
+    static constexpr size_t SMEM = (size_t)(2 * E + SLOTS + TWA + TWB + FA) * sizeof(float2) +
+                                   2 * sizeof(uint64_t) + 10 * sizeof(int64_t);
     static constexpr int MINB = T <= 256 ? 2 : 1;
     static_assert(LOG_WA >= 1 && LOG_WB >= 1, "a tile row must hold at least 16 bytes");
     // the stage exchange's barrier also orders the tile reads before the refill
@@ -88,10 +105,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
                                   PREC == PREC_FP32 ? FourStepShape<LOG_N1, LOG_N2, LOG_E>::MINB : 1)
     k_fourstep(const __grid_constant__ FourStepArgs a)
 {
-    // four-step table: exact [j2][k1] up to n = 2^20, else two factors with K = 64
-    constexpr bool TWO_LEVEL = LOG_N1 + LOG_N2 > 20;
-    constexpr int TW_LOG_K = TWO_LEVEL ? 6 : LOG_N1;
     using Sh = FourStepShape<LOG_N1, LOG_N2, LOG_E>;
+    constexpr int K = 1 << Sh::LOG_K;
     constexpr int N1 = Sh::N1, N2 = Sh::N2, E = Sh::E, T = Sh::T;
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
     constexpr int64_t N = (int64_t)N1 * N2;
@@ -99,7 +114,10 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
     extern __shared__ __align__(1024) float2 sm[];
     float2 *P = sm;  // two input tiles
     float2 *X = sm + 2 * E;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
+    float2 *TWA = X + Sh::SLOTS;  // stage tables (TW_SM)
+    float2 *TWB = LOG_N1 == LOG_N2 ? TWA : TWA + Sh::TWA;
+    float2 *F = TWA + Sh::TWA + Sh::TWB;  // [c][K + N1/K] four-step factors of the current A tile
+    uint64_t *bar = reinterpret_cast<uint64_t *>(F + Sh::FA);
     int64_t *item = reinterpret_cast<int64_t *>(bar + 2);  // [2]: the queue item held in P[b]
     int64_t *info = item + 2;                               // [2][4]: is_b, chunk, tile, segment
     const int tid = threadIdx.x;
@@ -196,6 +214,12 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    if constexpr (Sh::TW_SM) {
+        for (int e = tid; e < Sh::TWA; e += T) TWA[e] = __ldg(a.twA + e);
+        for (int e = tid; e < Sh::TWB; e += T) TWB[e] = __ldg(a.twB + e);
+    }
+    const float2 *twA = Sh::TW_SM ? TWA : a.twA;
+    const float2 *twB = Sh::TW_SM ? TWB : a.twB;
     __syncthreads();
     bool deferred[2] = {false, false};  // meaningful in thread 0 only
     if (tid == 0) {
@@ -238,6 +262,13 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
             // ---- A tile: columns j2 = ct*WA + cc of segment s, points j1 over N1
             const int ct = w % TA_SEG;
             if (valid) {
+                // the tile's four-step factors (read after the stage exchange's barrier)
+                for (int e = tid; e < Sh::FA; e += T) {
+                    const int cc = e / Sh::FK, q = e - cc * Sh::FK;
+                    const int64_t j2 = ct * WA + cc;
+                    F[e] = q < K ? __ldg(a.w4 + (j2 << Sh::LOG_K) + q)
+                                 : __ldg(a.w4hi + j2 * (N1 >> Sh::LOG_K) + (q - K));
+                }
                 gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int cc, int i) { return Pb[i * WA + cc]; });
                 if constexpr (PREC != PREC_FP32) {
                     __syncthreads();  // P[b] is about to hold tensor-core operands
@@ -245,7 +276,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
                 }
                 // (FP32: the stage exchange's barrier orders every read of P[b]
                 // before thread 0 refills it at the end of the iteration)
-                run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PS, 0, false, true, PREC>(v, X, a.twA, &tc);
+                run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PS, 0, false, true, PREC, false, Sh::TW_SM>(v, X, twA,
+                                                                                                     &tc);
                 // last stage in line-major order: this thread's outputs are
                 // k1 = j + (N1/R) r of column j2 = ct*WA + cc
                 using IL = StageInfo<LOG_N1, StageInfo<LOG_N1, 0>::NSTAGES - 1>;
@@ -256,22 +288,13 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
                     stage_coords<LOG_N1, Sh::LOG_WA, true, true, IL::NSTAGES - 1>(tid + T * bb, cc, j);
                     const int j2 = ct * WA + cc;
                     float2 *dst = a.ring + (int64_t)slab * N + (int64_t)j2 * N1 + j;
-                    if constexpr (TWO_LEVEL) {
-                        const float2 *w4 = a.w4 + ((int64_t)j2 << TW_LOG_K);
-                        const float2 *w4h = a.w4hi + (int64_t)j2 * (N1 >> TW_LOG_K);
+                    const float2 *Fc = F + cc * Sh::FK;
 #pragma unroll
-                        for (int r = 0; r < IL::R; ++r) {
-                            const int k1 = j + r * (N1 / IL::R);
-                            const float2 w1 = __ldg(w4 + (k1 & ((1 << TW_LOG_K) - 1)));
-                            const float2 w2 = __ldg(w4h + (k1 >> TW_LOG_K));
-                            const float2 wv = make_float2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
-                            dst[r * (N1 / IL::R)] = twmul<S>(v[bb * IL::R + r], wv);
-                        }
-                    } else {
-                        const float2 *w4 = a.w4 + (int64_t)j2 * N1 + j;
-#pragma unroll
-                        for (int r = 0; r < IL::R; ++r)
-                            dst[r * (N1 / IL::R)] = twmul<S>(v[bb * IL::R + r], __ldg(w4 + r * (N1 / IL::R)));
+                    for (int r = 0; r < IL::R; ++r) {
+                        const int k1 = j + r * (N1 / IL::R);
+                        const float2 w1 = Fc[k1 & (K - 1)], w2 = Fc[K + (k1 >> Sh::LOG_K)];
+                        const float2 wv = make_float2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
+                        dst[r * (N1 / IL::R)] = twmul<S>(v[bb * IL::R + r], wv);
                     }
                 }
             }
@@ -305,7 +328,8 @@ __global__ void __launch_bounds__(FourStepShape<LOG_N1, LOG_N2, LOG_E>::T,
                     __syncthreads();  // P[b] is about to hold tensor-core operands
                     tc.stage = P + b * E + warp * 512;
                 }
-                run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PS, 0, false, false, PREC>(v, X, a.twB, &tc);
+                run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PS, 0, false, false, PREC, false, Sh::TW_SM>(v, X, twB,
+                                                                                                      &tc);
                 using IL = StageInfo<LOG_N2, StageInfo<LOG_N2, 0>::NSTAGES - 1>;
                 constexpr int BL = 16 / IL::R;
 #pragma unroll

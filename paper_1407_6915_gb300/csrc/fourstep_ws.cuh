@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(FourStepWsShape<LOG_N1, LOG_N2, LOG_E>::TT, Fo
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
     constexpr int64_t N = (int64_t)N1 * N2;
     constexpr int TA_SEG = N2 / WA, TB_SEG = N1 / WB;
-    constexpr bool TWO_LEVEL = LOG_N1 + LOG_N2 > 20;
-    constexpr int TW_LOG_K = TWO_LEVEL ? 6 : LOG_N1;
+    constexpr int TW_LOG_K = Sh::LOG_K;  // four-step twiddle from two table factors
     extern __shared__ __align__(1024) float2 sm[];
     float2 *P = sm;
     float2 *X = sm + 2 * E;
@@ -331,14 +330,9 @@ __global__ void __launch_bounds__(FourStepWsShape<LOG_N1, LOG_N2, LOG_E>::TT, Fo
 #pragma unroll
                 for (int r = 0; r < IL::R; ++r) {
                     const int k1 = j + r * (N1 / IL::R);
-                    float2 wv;
-                    if constexpr (TWO_LEVEL) {
-                        const float2 w1 = __ldg(a.w4 + ((int64_t)j2 << TW_LOG_K) + (k1 & ((1 << TW_LOG_K) - 1)));
-                        const float2 w2 = __ldg(a.w4hi + (int64_t)j2 * (N1 >> TW_LOG_K) + (k1 >> TW_LOG_K));
-                        wv = make_float2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
-                    } else {
-                        wv = __ldg(a.w4 + (int64_t)j2 * N1 + k1);
-                    }
+                    const float2 w1 = __ldg(a.w4 + ((int64_t)j2 << TW_LOG_K) + (k1 & ((1 << TW_LOG_K) - 1)));
+                    const float2 w2 = __ldg(a.w4hi + (int64_t)j2 * (N1 >> TW_LOG_K) + (k1 >> TW_LOG_K));
+                    const float2 wv = make_float2(w1.x * w2.x - w1.y * w2.y, w1.x * w2.y + w1.y * w2.x);
                     Pb[(k1 / Sh::BOXY) * (Sh::BOXY * WA) + cc * Sh::BOXY + (k1 % Sh::BOXY)] =
                         twmul<S>(v[bb * IL::R + r], wv);
                 }

@@ -83,8 +83,8 @@ cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cud
         case 14: return fourstep_ws_s<7, 7, 12>(sign, a, st);
         case 15: return fourstep_ws_s<8, 7, 12>(sign, a, st);
         case 16: return fourstep_ws_s<8, 8, 12>(sign, a, st);
-        case 17: return fourstep_ws_s<9, 8, 13>(sign, a, st);
-        case 18: return fourstep_ws_s<9, 9, 13>(sign, a, st);
+        case 17: return fourstep_ws_s<9, 8, 12>(sign, a, st);
+        case 18: return fourstep_ws_s<9, 9, 12>(sign, a, st);
         case 19: return fourstep_ws_s<10, 9, 13>(sign, a, st);
         case 20: return fourstep_ws_s<10, 10, 13>(sign, a, st);
         case 21: return fourstep_ws_s<11, 10, 13>(sign, a, st);
@@ -100,7 +100,7 @@ bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_w
     if (log_n < 14 || log_n > 24) return false;
     *log_n1 = (log_n + 1) / 2;
     *log_n2 = log_n / 2;
-    const int log_e = *log_n1 <= 8 ? 12 : 13;
+    const int log_e = *log_n1 <= 9 ? 12 : 13;  // 4096-point tiles (two CTAs per SM) up to N1 = 512
     *log_wa = log_e - *log_n1;
     *log_wb = log_e - *log_n2;
     return true;
@@ -120,8 +120,8 @@ cudaError_t launch_fourstep(int log_n, int sign, int prec, const FourStepArgs &a
         case 14: return fourstep_s<7, 7, 12>(sign, a, st);
         case 15: return fourstep_s<8, 7, 12>(sign, a, st);
         case 16: return fourstep_s<8, 8, 12>(sign, a, st);
-        case 17: return fourstep_s<9, 8, 13>(sign, a, st);
-        case 18: return fourstep_s<9, 9, 13>(sign, a, st);
+        case 17: return fourstep_s<9, 8, 12>(sign, a, st);
+        case 18: return fourstep_s<9, 9, 12>(sign, a, st);
         case 19: return fourstep_s<10, 9, 13>(sign, a, st);
         case 20: return fourstep_s<10, 10, 13>(sign, a, st);
         case 21: return fourstep_s<11, 10, 13>(sign, a, st);

@@ -36,5 +36,8 @@ struct FourStepWsArgs;
 cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
+// The four-step twiddle w_n^{j2 k1} is the product of two table entries,
+// w_n^{j2 (k1 mod K)} and w_n^{j2 K (k1 div K)}, with K = 2^fourstep_log_k(log2 N1).
+__host__ __device__ constexpr int fourstep_log_k(int log_n1) { return log_n1 / 2; }
 
 }  // namespace fftseg

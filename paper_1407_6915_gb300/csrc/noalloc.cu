@@ -17,14 +17,16 @@ constexpr int kNaMinLogN = 17, kNaMaxLogN = 20;
 constexpr int64_t kNaChunkBytes = 8ll << 20;                      // one ring chunk
 constexpr int kNaRing = 3;                                         // chunks in the ring
 constexpr int64_t kNaRingElems = kNaRing * kNaChunkBytes / 8;      // float2 elements
-constexpr int64_t kNaW4Elems = int64_t(1) << kNaMaxLogN;           // [j2][k1] table
+constexpr int64_t kNaW4Elems = int64_t(1) << 16;                   // [j2][k1 mod K] (2^15 used at n = 2^20)
+constexpr int64_t kNaW4hiElems = int64_t(1) << 16;                 // [j2][k1 div K] (2^15 used at n = 2^20)
 constexpr int64_t kNaStageElems = 1024;                            // stage tables of one line (< 1024 entries)
 constexpr int kNaMaxChunks = 65536;                                // chunks per launch
 constexpr int64_t kNaCtrElems = (1 + 2 * (int64_t)kNaMaxChunks + 1 + 1) / 2;  // counters + flag, as float2 slots
 
 constexpr int64_t kNaOffRing = 0;
 constexpr int64_t kNaOffW4 = kNaOffRing + kNaRingElems;
-constexpr int64_t kNaOffStageA = kNaOffW4 + kNaW4Elems;
+constexpr int64_t kNaOffW4hi = kNaOffW4 + kNaW4Elems;
+constexpr int64_t kNaOffStageA = kNaOffW4hi + kNaW4hiElems;
 constexpr int64_t kNaOffStageB = kNaOffStageA + kNaStageElems;
 constexpr int64_t kNaOffCtr = kNaOffStageB + kNaStageElems;
 constexpr int64_t kNaElems = kNaOffCtr + kNaCtrElems;
@@ -32,7 +34,7 @@ constexpr int64_t kNaElems = kNaOffCtr + kNaCtrElems;
 }  // namespace
 }  // namespace fftseg
 
-// 8 B * (3 Mi + 1 Mi + 2 Ki + 64 Ki) elements = about 32.5 MiB per GPU.
+// 8 B * (3 Mi + 128 Ki + 2 Ki + 64 Ki) elements = about 25.5 MiB per GPU.
 static __device__ __align__(256) float2 g_noalloc_scratch[fftseg::kNaElems];
 
 namespace fftseg {
@@ -69,13 +71,19 @@ __device__ void stage_entry(float2 *tab, int log_l, int idx)
     }
 }
 
+// Four-step factor tables (w_n^{j2 k1} = lo[j2][k1 mod K] * hi[j2][k1 div K])
+// and the stage tables of both line lengths.
 __global__ void k_noalloc_tables(float2 *scratch, int log_n1, int log_n2)
 {
+    const int log_k = fourstep_log_k(log_n1);
     const int64_t n1 = int64_t(1) << log_n1, n2 = int64_t(1) << log_n2, n = n1 * n2;
-    float2 *w4 = scratch + kNaOffW4;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j2 = e / n1, k1 = e % n1;  // [j2][k1] = w_n^{j2 k1}
-        w4[e] = root_fwd(j2 * k1, n);
+    const int64_t K = int64_t(1) << log_k, nhi = n1 >> log_k;
+    float2 *lo = scratch + kNaOffW4, *hi = scratch + kNaOffW4hi;
+    const int64_t count = n2 * (K > nhi ? K : nhi);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count || e < kNaStageElems;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < n2 * K) lo[e] = root_fwd((e >> log_k) * (e & (K - 1)), n);
+        if (e < n2 * nhi) hi[e] = root_fwd((e / nhi) * K * (e % nhi), n);
         if (e < kNaStageElems) {
             stage_entry(scratch + kNaOffStageA, log_n1, (int)e);
             stage_entry(scratch + kNaOffStageB, log_n2, (int)e);
@@ -156,14 +164,14 @@ extern "C" int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int
         a.twA = base + kNaOffStageA;
         a.twB = base + kNaOffStageB;
         a.w4 = base + kNaOffW4;
-        a.w4hi = nullptr;
+        a.w4hi = base + kNaOffW4hi;
         a.ctr = ctr;
         a.err = ctr + 1 + 2 * kNaMaxChunks;
         a.nseg = cnt;
         a.nchunks = (int)nc;
         a.cs = (int)cs;
         a.nr = kNaRing;
-        a.log_k = l1;
+        a.log_k = fourstep_log_k(l1);
         a.out_power = 0;
         a.scale = scale;
         e = cudaMemsetAsync(ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);  // queue head and chunk counters

@@ -132,8 +132,8 @@ void free_plan(fftseg_plan p)
     delete p;
 }
 
-// Persistent four-step: ring, counters, stage tables and the transposed
-// four-step table [j2][k1] (split in two for n > 2^20).
+// Persistent four-step: ring, counters, stage tables and the two factor
+// tables of the four-step twiddle, [j2][k1 mod K] and [j2][k1 div K].
 int build_fourstep(fftseg_plan p)
 {
     int l1, l2, lwa, lwb;
@@ -148,7 +148,7 @@ int build_fourstep(fftseg_plan p)
     int rc;
     if ((rc = stage_table(&p->twA, n1))) return rc;
     if ((rc = stage_table(&p->twB, n2))) return rc;
-    p->w4_log_k = p->log_n > kTwoLevelAbove ? kTwLogK : l1;
+    p->w4_log_k = fourstep_log_k(l1);
     const int64_t K = int64_t(1) << p->w4_log_k;
     {
         std::vector<float2> h((size_t)(n2 * K));

@@ -88,8 +88,8 @@ def test_poll_times_out_instead_of_blocking():
     x = torch.zeros(nseg, n, dtype=torch.complex64, device="cuda")
     y = torch.empty_like(x)
     ids = [srv.submit(x, y, n, nseg) for _ in range(4)]
-    done, _ = srv.poll(ids[-1], timeout_us=1)  # 512 MiB x 4 cannot be done in 1 us
-    assert not done
+    done, st = srv.poll(ids[-1], timeout_us=1)  # 512 MiB x 4 cannot be done in 1 us
+    assert not done, (st, fs.last_error(), srv.stats())
     for jid in ids:
         assert srv.poll(jid, timeout_us=60_000_000) == (True, fs.OK)
     with pytest.raises(fs.FFTSegError):
