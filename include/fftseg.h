@@ -70,6 +70,9 @@ enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
                                              compute warps (TMA loads and stores) */
 /* single-pass cluster path: request a cluster of 2^c CTAs (0 = the library's choice) */
 #define FFTSEG_FLAG_CLUSTER_LOG2(c) (((unsigned)(c) & 0xFu) << 8)
+/* time every schedule built for n on the current GPU at plan creation and use
+   the fastest (replaces the schedule flags above; see fftseg_autotune) */
+#define FFTSEG_FLAG_AUTOTUNE 0x10u
 
 #define FFTSEG_MAX_LOG2N 24
 
@@ -133,6 +136,22 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
  * out[0] read callback, out[1] H2D, out[2] transform, out[3] D2H,
  * out[4] write callback, out[5] wall time. */
 int fftseg_stream_phases(fftseg_plan p, double out[6]);
+
+/*
+ * Autotuner (the schedule choice that the paper leaves to its FFT library):
+ * where more than one schedule is built for n (cluster sizes 2..16 CTAs, the
+ * persistent four-step with or without a producer warp, the two-pass form),
+ * each is timed on the current GPU over min(batch, 256 MiB of input) zero
+ * segments and the fastest is returned as plan flags in *flags_out (0 where
+ * one schedule exists), with its time per exec in *ms_out (may be NULL; < 0
+ * when nothing was timed).  Choices are cached for the process, keyed by GPU
+ * name, SM count, n, precision, output kind and the timed segment count; if
+ * the environment variable FFTSEG_TUNE_CACHE names a file, choices are read
+ * from it on first use and new ones appended.  Synchronous; allocates
+ * scratch for the timing.  A plan created with FFTSEG_FLAG_AUTOTUNE makes
+ * this call itself.
+ */
+int fftseg_autotune(int64_t n, int64_t batch, int precision, int out_kind, unsigned *flags_out, double *ms_out);
 
 /*
  * A batch held in host memory through a chain of plans (Sec. III's copy in,

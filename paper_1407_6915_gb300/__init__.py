@@ -22,6 +22,7 @@ NORM_NONE, NORM_BACKWARD, NORM_ORTHO = 0, 1, 2
 PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
 OUT_COMPLEX, OUT_POWER = 0, 1
 FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2, FLAG_FOURSTEP_PRODUCER = 0x1, 0x2, 0x4, 0x8
+FLAG_AUTOTUNE = 0x10
 
 
 PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step"}
@@ -69,6 +70,8 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "fftseg_autotune": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_double)]),
     "fftseg_exec_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
     "fftseg_exec_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
@@ -127,6 +130,16 @@ def _stream_handle(stream):
 
 def _ptr(t):
     return t if isinstance(t, int) else t.data_ptr()
+
+
+def autotune(n, batch, precision=None, out_kind=None):
+    """fftseg_autotune: (schedule flags, ms per exec) of the fastest schedule for n."""
+    precision = PREC_FP32 if precision is None else precision
+    out_kind = OUT_COMPLEX if out_kind is None else out_kind
+    flags, ms = ctypes.c_uint(0), ctypes.c_double(0.0)
+    check(lib().fftseg_autotune(int(n), int(batch), precision, out_kind, ctypes.byref(flags), ctypes.byref(ms)),
+          "fftseg_autotune")
+    return flags.value, ms.value
 
 
 def exec_host(plans, h_in, h_out, nseg, chunk_segments=0) -> None:

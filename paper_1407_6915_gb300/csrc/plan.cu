@@ -481,6 +481,12 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
         return set_error(FFTSEG_E_INVALID, "plan_create: bad precision %d", precision);
     if (batch > (int64_t(1) << 40) / n)
         return set_error(FFTSEG_E_INVALID, "plan_create: batch*n too large");
+    if (flags & FFTSEG_FLAG_AUTOTUNE) {  // replace the schedule flags by the fastest measured schedule
+        unsigned chosen = 0;
+        const int trc = tune_schedule(n, batch, precision, out_kind, &chosen, nullptr);
+        if (trc != FFTSEG_OK) return trc;
+        flags = (flags & ~(kPathFlags | FFTSEG_FLAG_AUTOTUNE)) | chosen;
+    }
 
     fftseg_plan p = new (std::nothrow) fftseg_plan_s();
     if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");

@@ -63,6 +63,14 @@ void count_launches(int64_t k);
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
                    int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes = 8);
 
+// Plan flags that select a schedule (the rest are options).
+constexpr unsigned kPathFlags = FFTSEG_FLAG_FORCE_TWOPASS | FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_PRODUCER |
+                                FFTSEG_FLAG_CLUSTER_LOG2(0xF);
+
+// Autotuner (tune.cu): the schedule flags of the fastest schedule for n on
+// the current GPU, timed on min(batch, 256 MiB of input) segments.
+int tune_schedule(int64_t n, int64_t batch, int prec, int out_kind, unsigned *flags_out, double *ms_out);
+
 // Run the plan on nseg segments (arguments already validated).
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);
 

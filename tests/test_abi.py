@@ -66,7 +66,25 @@ def test_null_arguments_are_errors_not_crashes():
     assert L.fftseg_stream(None, None, None, None, None, 0, 0, 0, ctypes.byref(committed)) == fs.E_INVALID
     assert L.fftseg_plan_info(None, None) == fs.E_INVALID
     assert L.fftseg_stream_phases(None, None) == fs.E_INVALID
+    assert L.fftseg_exec_host(None, 0, None, None, 1, 0) == fs.E_INVALID
+    assert L.fftseg_autotune(1024, 1, 0, 0, None, None) == fs.E_INVALID
+    flags = ctypes.c_uint(0)
+    assert L.fftseg_autotune(1000, 1, 0, 0, ctypes.byref(flags), None) == fs.E_UNSUPPORTED
+    assert L.fftseg_autotune(1024, 0, 0, 0, ctypes.byref(flags), None) == fs.E_INVALID
     assert isinstance(fs.launch_count(), int)
+
+
+def test_binding_constants_match_the_header():
+    text = open(os.path.join(ROOT, "include", "fftseg.h")).read()
+    defines = {m.group(1): int(m.group(2), 16) for m in
+               re.finditer(r"#define\s+FFTSEG_(FLAG_\w+)\s+(0x[0-9a-fA-F]+)u", text)}
+    assert defines, "no flag defines found"
+    for name, value in defines.items():
+        assert getattr(fs, name) == value, name
+    for name in ("OK", "E_INVALID", "E_NOMEM", "E_CUDA", "E_IO", "E_PARTIAL", "E_TIMEOUT", "E_UNSUPPORTED"):
+        m = re.search(r"FFTSEG_%s\s*=\s*(-?\d+)" % name, text)
+        assert m and int(m.group(1)) == getattr(fs, name), name
+    assert fs.FLAG_CLUSTER_LOG2(3) == 3 << 8
 
 
 def test_paper_record_arithmetic():
