@@ -248,7 +248,9 @@ def stream_bench(link, h_signal=None):
 
 def tc_split(peak):
     """FP32 versus tensor-core (split hi+lo FP16 / BF16) on the same GPU: time of one
-    4 GiB batch and relative L2 error against the FP64 oracle on a sample of segments."""
+    4 GiB batch (uniform input) and relative L2 error against the FP64 oracle on a
+    sample of segments, for both input families (uniform seed 3, tones + noise seed 4:
+    one 2^29-sample signal each, cut into segments of every size)."""
     import torch
     import numpy as np
     import oracle
@@ -256,18 +258,28 @@ def tc_split(peak):
     import siggen
     out = []
     sample = {12: 64, 16: 8, 20: 2, 24: 1}
+    count = 1 << 29
+    fam = {}
+    for name, kind, seed in (("uniform", siggen.KIND_UNIFORM, 3), ("tones", siggen.KIND_TONES, 4)):
+        h = torch.empty(count, dtype=torch.complex64, pin_memory=True)
+        siggen.fill_pointer(kind, seed, 0, count, h.data_ptr())
+        fam[name] = (h, h.cuda())
     for log_n in (12, 16, 20, 24):
         n = 1 << log_n
-        B = (1 << 29) // n
-        h = torch.empty(B * n, dtype=torch.complex64, pin_memory=True)
-        siggen.fill_pointer(siggen.KIND_UNIFORM, 3, 0, B * n, h.data_ptr())
-        x = h.cuda().view(B, n)
-        y = torch.empty_like(x)
+        B = count // n
         k = sample[log_n]
-        ref = oracle.fft(h[:k * n].numpy().reshape(k, n), oracle.FORWARD)
+        refs = {f: oracle.fft(h[:k * n].numpy().reshape(k, n), oracle.FORWARD) for f, (h, _) in fam.items()}
+        y = torch.empty(B, n, dtype=torch.complex64, device="cuda")
         row = {"n": n, "segments": B}
         for name, prec in (("fp32", fs.PREC_FP32), ("tc_fp16", fs.PREC_TC_FP16), ("tc_bf16", fs.PREC_TC_BF16)):
             plan = fs.Plan(n, B, fs.FORWARD, precision=prec)
+            errs = {}
+            for f, (_, d) in fam.items():
+                plan.exec(d.view(B, n), out=y)
+                torch.cuda.synchronize()
+                got = y[:k].cpu().numpy().astype(np.complex128)
+                errs[f] = float(np.linalg.norm((got - refs[f]).ravel()) / np.linalg.norm(refs[f].ravel()))
+            x = fam["uniform"][1].view(B, n)
             for _ in range(3):
                 plan.exec(x, out=y)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -279,18 +291,38 @@ def tc_split(peak):
             torch.cuda.synchronize()
             plan.check()
             ms = e0.elapsed_time(e1) / reps
-            got = y[:k].cpu().numpy().astype(np.complex128)
-            err = float(np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()))
             gbs = 16.0 * n * B / (ms / 1e3) / 1e9
             row[name] = {"ms": round(ms, 4), "gflops": round(flops_per_transform(n, B) / (ms / 1e3) / 1e9, 1),
-                         "hbm_frac": round(gbs / peak, 4), "rel_l2": err, "path": plan.info()["path"]}
+                         "hbm_frac": round(gbs / peak, 4), "rel_l2_uniform": errs["uniform"],
+                         "rel_l2_tones": errs["tones"], "path": plan.info()["path"]}
             del plan
         out.append(row)
-        del x, y, h
+        del y
         torch.cuda.empty_cache()
-    return {"batch_bytes": 1 << 32, "input": "uniform[-1,1), seed 3",
+    del fam
+    torch.cuda.empty_cache()
+    return {"batch_bytes": 1 << 32, "timed_input": "uniform[-1,1), seed 3",
+            "rel_l2_inputs": "uniform seed 3; 32 tones + noise seed 4",
             "rel_l2_sample_segments": {str(1 << k): v for k, v in sample.items()},
             "bound_fp32": "2e-6*log2(n)", "bound_tc": 1e-4, "sizes": out}
+
+
+def tune_table():
+    """The autotuner's choice per length (FP32, complex output, a 256 MiB batch)
+    beside the library's default schedule."""
+    import paper_1407_6915_gb300 as fs
+    rows = []
+    for log_n in range(13, 25):
+        n = 1 << log_n
+        flags, ms = fs.autotune(n, max(1, (1 << 25) // n))
+        plan = fs.Plan(n, 1, fs.FORWARD)
+        default = plan.info()["path"]
+        plan.destroy()
+        plan = fs.Plan(n, 1, fs.FORWARD, flags=flags)
+        rows.append({"n": n, "tuned_flags": hex(flags), "tuned_path": plan.info()["path"],
+                     "tuned_ms_per_256mib": round(ms, 4), "default_path": default})
+        plan.destroy()
+    return rows
 
 
 def serve_bench(peak, njobs=600, seed=5):
@@ -539,7 +571,8 @@ def run_ours(args):
                              "mean_launch_ms": round(per_launch_ms, 4)},
                 "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
                         "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2),
-                        "step_ms": e2e_step_ms, "warmup_calls": args.warmup, "call": "fftseg_exec_host([forward, inverse]) on pinned host buffers",
+                        "step_ms": e2e_step_ms, "median_step_ms": round(statistics.median(e2e_step_ms), 2),
+                        "warmup_calls": args.warmup, "call": "fftseg_exec_host([forward, inverse]) on pinned host buffers",
                         "link_gbs_each_way": round(x.numel() * 8 / e2e_s / 1e9, 1),
                         "link_peaks_gbs": link,
                         "link_frac": round(x.numel() * 8 / e2e_s / 1e9 / link["concurrent_each_way"], 4),
@@ -554,6 +587,7 @@ def run_ours(args):
             torch.cuda.empty_cache()
             line["stream"] = stream_bench(link, h_in)
             line["tc_split"] = tc_split(peak)
+            line["autotune"] = tune_table()
             line["serve"] = serve_bench(peak)
     if world > 1:
         import torch.distributed as dist

@@ -233,17 +233,21 @@ int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int64_t nseg, 
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching of segment-FFT jobs of different lengths.  Jobs are
- * admitted while the bytes they touch fit the HBM budget and fewer than
- * max_inflight_jobs run; admitted jobs are grouped by length, and each group
- * runs in one persistent ragged kernel launch (replayed from a captured CUDA
- * graph per length bucket) on the server's stream.  Plans and twiddles stay
+ * admitted in arrival order while the bytes they touch fit the HBM budget and
+ * fewer than max_inflight_jobs run (a job larger than the budget is admitted
+ * in pieces of whole segments).  Each admission round runs every admitted
+ * job with n <= 4096 in one persistent ragged kernel launch (a captured CUDA
+ * graph replayed from one of two slots), and every piece of a longer job
+ * through a resident plan of its length on one of four lane streams, so that
+ * rounds and large pieces overlap on the device.  Plans and twiddles stay
  * resident.  A job's result is the same alone and in any mix.
  */
 typedef struct fftsrv_s *fftsrv;
 typedef struct {
     int64_t hbm_budget_bytes; /* bytes of job input+output that may be in flight */
     int max_inflight_jobs;
-    fftseg_stream_t stream;   /* NULL: the server creates its own stream */
+    fftseg_stream_t stream;   /* NULL: the server creates its own streams (four lanes for
+                                 large jobs); else large jobs run in order on this stream */
 } fftsrv_config;
 typedef struct {
     const void *d_in; /* [nseg][n] complex64, device */

@@ -13,7 +13,10 @@
 //    slot and replayed; two slots on two streams let consecutive rounds
 //    overlap on the device;
 //  - every piece of a larger job through a resident plan of its length
-//    (cluster or persistent four-step kernels) on a third stream.
+//    (cluster or persistent four-step kernels) on one of four more streams
+//    (lanes), round-robin, each lane with plans of its own, so that pieces
+//    of several large jobs overlap on the device (a caller-given stream is
+//    the single lane instead).
 // Completion is reported by host callbacks queued behind each launch; they
 // release the job's bytes, wake the scheduler and wake fftsrv_poll.
 #include <chrono>
@@ -33,6 +36,7 @@ namespace fftseg {
 namespace {
 
 constexpr int kMaxItems = 1024;  // small jobs (pieces) per ragged round
+constexpr int kLanes = 4;        // streams for the pieces of large jobs
 constexpr int kSmallMaxLog = 12;
 
 struct RaggedItem {
@@ -185,14 +189,15 @@ void CUDART_CB on_done(void *arg);
 struct fftsrv_s {
     fftsrv_config cfg{};
     int device = 0;
-    cudaStream_t s_large = nullptr;
+    cudaStream_t s_large[kLanes] = {};
+    int nlanes = 1, next_lane = 0;
     bool own_large = false;
     Slot slots[2];
     int next_slot = 0;
     float2 *d_tw = nullptr;  // small-n stage tables, log_n = 1..12
     int64_t tw_off[kSmallMaxLog + 1] = {};
     int *d_err = nullptr;
-    std::map<std::pair<int, int>, fftseg_plan> plans;  // (log_n, direction*4+norm) for n > 4096
+    std::map<std::pair<int, int>, fftseg_plan> plans;  // (log_n, (direction*4+norm)*kLanes+lane), n > 4096
     std::mutex mu;
     std::condition_variable cv_sched, cv_done;
     std::deque<uint64_t> pending;
@@ -208,9 +213,9 @@ struct fftsrv_s {
 
     // Resident plan for length 2^log_n; its batch covers the largest piece any
     // job of that length can be cut into (an in-place job counts n*8 bytes a segment).
-    fftseg_plan plan_for(int log_n, int direction, int norm, int *rc)
+    fftseg_plan plan_for(int log_n, int direction, int norm, int lane, int *rc)
     {
-        const std::pair<int, int> key(log_n, direction * 4 + norm);
+        const std::pair<int, int> key(log_n, (direction * 4 + norm) * kLanes + lane);
         auto it = plans.find(key);
         if (it != plans.end()) return it->second;
         fftseg_plan p = nullptr;
@@ -366,11 +371,13 @@ void fftsrv_s::scheduler()
                 continue;
             }
             const int64_t n = int64_t(1) << jb.log_n;
-            fftseg_plan p = plan_for(jb.log_n, jb.j.direction, jb.j.norm, &rc);
+            const int lane = next_lane;
+            next_lane = (next_lane + 1) % nlanes;
+            fftseg_plan p = plan_for(jb.log_n, jb.j.direction, jb.j.norm, lane, &rc);
             const int64_t before = fftseg_launch_count();
             if (rc == FFTSEG_OK)
                 rc = exec_plan(p, static_cast<const float2 *>(jb.j.d_in) + seg0 * n,
-                               static_cast<float2 *>(jb.j.d_out) + seg0 * n, cnt, s_large);
+                               static_cast<float2 *>(jb.j.d_out) + seg0 * n, cnt, s_large[lane]);
             if (rc != FFTSEG_OK) {
                 failed.push_back(piece);
                 continue;
@@ -379,7 +386,7 @@ void fftsrv_s::scheduler()
                 std::lock_guard<std::mutex> g(mu);
                 launches += fftseg_launch_count() - before;
             }
-            hand_over(s_large, new Done{this, {piece}});
+            hand_over(s_large[lane], new Done{this, {piece}});
         }
         lock.lock();
         if (!failed.empty()) {  // their jobs end with the error; their bytes are released
@@ -420,9 +427,12 @@ int fftsrv_create(fftsrv *out, const fftsrv_config *cfg)
         if (e != cudaSuccess && rc == FFTSEG_OK) rc = cuda_error(e, what); \
     } while (0)
     if (cfg->stream) {
-        s->s_large = reinterpret_cast<cudaStream_t>(cfg->stream);
+        s->s_large[0] = reinterpret_cast<cudaStream_t>(cfg->stream);
+        s->nlanes = 1;
     } else {
-        SRV_CHECK(cudaStreamCreateWithFlags(&s->s_large, cudaStreamNonBlocking), "fftsrv_create: stream");
+        for (int i = 0; i < kLanes; ++i)
+            SRV_CHECK(cudaStreamCreateWithFlags(&s->s_large[i], cudaStreamNonBlocking), "fftsrv_create: stream");
+        s->nlanes = kLanes;
         s->own_large = true;
     }
     // small-n stage tables
@@ -569,9 +579,11 @@ int fftsrv_destroy(fftsrv s)
         cudaFree(sl.d_cursor);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
-    if (s->s_large) cudaStreamSynchronize(s->s_large);
+    for (int i = 0; i < kLanes; ++i)
+        if (s->s_large[i]) cudaStreamSynchronize(s->s_large[i]);
     for (auto &kv : s->plans) fftseg_plan_destroy(kv.second);
-    if (s->own_large && s->s_large) cudaStreamDestroy(s->s_large);
+    for (int i = 0; i < kLanes; ++i)
+        if (s->own_large && s->s_large[i]) cudaStreamDestroy(s->s_large[i]);
     cudaFree(s->d_tw);
     cudaFree(s->d_err);
     delete s;
