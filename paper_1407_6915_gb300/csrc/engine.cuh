@@ -278,6 +278,13 @@ FDEV void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Release add at GPU scope: this thread's earlier memory operations, and those
+// it has observed through synchronisation, are visible before the add.
+FDEV void red_release_add(int *p, int v)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Drop a 128-byte line from L2 without writing it back (its contents become
 // undefined): for intermediate data that has been consumed.
 FDEV void discard_l2_line(const void *p) { asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory"); }
@@ -308,6 +315,34 @@ FDEV void tma_load_3d(void *dst, const CUtensorMap *tmap, int x, int y, int z, u
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
+}
+
+// L2 cache policy: lines fetched or written under it are evicted first (for
+// data streamed once, so that it does not displace data kept in L2).
+FDEV uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// tma_load_3d with an L2 cache policy
+FDEV void tma_load_3d_hint(void *dst, const CUtensorMap *tmap, int x, int y, int z, uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
+// tma_store_3d with an L2 cache policy
+FDEV void tma_store_3d_hint(const CUtensorMap *tmap, int x, int y, int z, const void *src, uint64_t policy)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2, %3}], [%4], %5;" ::"l"(
+                     reinterpret_cast<uint64_t>(tmap)),
+                 "r"(x), "r"(y), "r"(z), "r"(smem_u32(src)), "l"(policy)
+                 : "memory");
 }
 
 // address of the same shared-memory variable in CTA `rank` of the cluster
@@ -372,6 +407,23 @@ FDEV bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
+
+// Non-blocking test of phase `parity` of *bar.
+FDEV bool mbar_test_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// GPU-scope acquire-release fence.
+FDEV void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 // Wait for phase `parity` of *bar; false (and *err set) if it never completes.
 FDEV bool mbar_wait(uint64_t *bar, uint32_t parity, int *err)

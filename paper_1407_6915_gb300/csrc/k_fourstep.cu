@@ -1,6 +1,7 @@
 // Instantiations and launcher of the persistent L2 four-step kernel (n = 2^14..2^24).
 #include "fourstep.cuh"
 #include "fourstep_ws.cuh"
+#include "fourstep_hw.cuh"
 #include "launch.h"
 
 namespace fftseg {
@@ -44,6 +45,29 @@ cudaError_t fourstep_tc(int sign, int prec, const FourStepArgs &a, cudaStream_t 
                         : fourstep_t<LOG_N1, LOG_N2, LOG_E, 1, PREC_FP16>(a, st);
     return sign < 0 ? fourstep_t<LOG_N1, LOG_N2, LOG_E, -1, PREC_BF16>(a, st)
                     : fourstep_t<LOG_N1, LOG_N2, LOG_E, 1, PREC_BF16>(a, st);
+}
+
+template <int S>
+cudaError_t fourstep_hw_t(const FourStepHwArgs &a, cudaStream_t st)
+{
+    using Sh = FourStepHwShape;
+    auto k = k_fourstep_hw<S>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Sh::TT, Sh::SMEM);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) return cudaErrorLaunchOutOfResources;
+        per_sm = occ;
+    }
+    const int64_t items = (int64_t)a.nchunks * a.cs * 2 * Sh::TILES_SEG;
+    int64_t grid = (int64_t)per_sm * device_sm_count();
+    if (grid > items) grid = items;
+    if (grid < 1) return cudaSuccess;
+    k<<<(unsigned)grid, Sh::TT, Sh::SMEM, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <int LOG_N1, int LOG_N2, int LOG_E, int S>
@@ -93,6 +117,11 @@ cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cud
         case 24: return fourstep_ws_s<12, 12, 13>(sign, a, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t st)
+{
+    return sign < 0 ? fourstep_hw_t<-1>(a, st) : fourstep_hw_t<1>(a, st);
 }
 
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb)

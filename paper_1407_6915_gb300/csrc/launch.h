@@ -34,6 +34,10 @@ cudaError_t launch_fourstep(int log_n, int sign, int prec, const FourStepArgs &a
 // loads and stores.
 struct FourStepWsArgs;
 cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cudaStream_t st);
+// Half-warp-line persistent four-step kernel for n = 65536 (FP32, complex
+// output): producer warp, three swizzled TMA tile buffers, TMA output stores.
+struct FourStepHwArgs;
+cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

@@ -11,6 +11,7 @@
 #include "fourstep.cuh"
 #include "fourstep_ws.cuh"
 #include "launch.h"
+#include "fourstep_hw.cuh"
 #include "plan.h"
 
 namespace fftseg {
@@ -26,6 +27,14 @@ constexpr int64_t kChunkBytes = 16ll << 20;  // four-step chunk; the ring holds 
 constexpr int kRingNr = 3;
 
 bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+// The persistent four-step path runs on the warp-local-line kernel for
+// n = 256 x 256 with FP32 arithmetic and complex output.
+bool uses_fourstep_hw(const fftseg_plan_s *p)
+{
+    return p->log_n == 16 && p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
+           !(p->flags & FFTSEG_FLAG_FOURSTEP_PRODUCER);
+}
 int ilog2(int64_t n)
 {
     int l = 0;
@@ -164,11 +173,12 @@ int build_fourstep(fftseg_plan p)
     if (cs < 1) cs = 1;
     if (cs > p->batch) cs = p->batch;
     p->ring_cs = (int)cs;
-    p->ring_nr = kRingNr;
+    p->ring_nr = uses_fourstep_hw(p) ? FourStepHwShape::MIN_RING : kRingNr;
     cudaError_t e = cudaMalloc((void **)&p->ring, (size_t)(p->ring_nr * cs * p->n) * sizeof(float2));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(ring)");
     const int64_t nc = (p->batch + cs - 1) / cs;
-    p->ctr_count = 1 + 2 * nc;
+    // counters per chunk, or per segment for the warp-local-line kernel
+    p->ctr_count = 1 + 2 * (uses_fourstep_hw(p) ? nc * cs : nc);
     e = cudaMalloc((void **)&p->ctr, (size_t)p->ctr_count * sizeof(int));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(counters)");
     return FFTSEG_OK;
@@ -211,9 +221,13 @@ int build_fp32(fftseg_plan p)
     }
     int l1, l2, lc;
     const int want_c = (int)((p->flags >> 8) & 0xFu);
-    // measured on GB300: the cluster path wins up to 2^16, the persistent
-    // four-step above (a 16-CTA cluster per 2^17 segment leaves SMs idle)
-    if (!force2 && want_c == 0 && ln >= 17) return build_fourstep(p);
+    // measured on GB300: the cluster path wins up to 2^15 (and for |X|^2
+    // output at 2^16), the persistent four-step above: at 2^16 its
+    // warp-local-line kernel (16384 segments: 4.3 ms against 5.5 ms for
+    // 16-CTA clusters, whose all-to-all exchange is bound by the SM-to-SM
+    // network), from 2^17 on because a 16-CTA cluster per segment leaves SMs idle
+    if (!force2 && want_c == 0 && (ln >= 17 || (ln == 16 && p->out_kind == FFTSEG_OUT_COMPLEX)))
+        return build_fourstep(p);
     if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: no cluster of 2^%d CTAs is built for n=2^%d",
                          want_c, ln);
@@ -265,7 +279,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
 }  // namespace
 
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
-                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes)
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, bool swizzle128)
 {
     const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
     const cuuint64_t strides[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
@@ -284,7 +298,9 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
     }
     CUresult r = encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
                         const_cast<void *>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return FFTSEG_OK;
@@ -417,6 +433,33 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
                 e = launch_fourstep_ws(p->log_n, sign, a, st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
+                count_launches(1);
+                return FFTSEG_OK;
+            }
+            if (uses_fourstep_hw(p)) {
+                // n = 256 x 256: warp-local lines, loader and retirer warps, TMA output stores
+                FourStepHwArgs a{};
+                const int64_t slabs = (int64_t)p->ring_nr * p->ring_cs;
+                int rc = encode_tmap_3d(&a.tmA, in, 256, 256, nseg, 256 * 8, n * 8, 16, 256, 8, true);
+                if (rc == FFTSEG_OK) rc = encode_tmap_3d(&a.tmB, p->ring, 256, 256, slabs, 256 * 8, n * 8, 16, 256, 8, true);
+                if (rc == FFTSEG_OK) rc = encode_tmap_3d(&a.tmO, d_out, 256, 256, nseg, 256 * 8, n * 8, 16, 256, 8, true);
+                if (rc != FFTSEG_OK) return rc;
+                const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+                a.ring = p->ring;
+                a.twL = p->twA;
+                a.w4 = p->w4;
+                a.w4hi = p->w4hi;
+                a.ctr = p->ctr;
+                a.err = p->d_err;
+                a.nseg = nseg;
+                a.nchunks = (int)nc;
+                a.cs = p->ring_cs;
+                a.nr = p->ring_nr;
+                a.scale = p->scale;
+                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * p->ring_cs) * sizeof(int), st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+                e = launch_fourstep_hw(sign, a, st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
                 count_launches(1);
                 return FFTSEG_OK;

@@ -60,8 +60,10 @@ void count_launches(int64_t k);
 
 // Tensor map over 8-byte (or 4-byte) elements: dims (d0 innermost, d1, d2),
 // byte strides of dims 1 and 2, box (box0, box1, 1).
+// swizzle128: the box lands in shared memory with the 128-byte swizzle (box0 *
+// elem_bytes must be 128; the shared destination 1024-byte aligned).
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
-                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes = 8);
+                   int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes = 8, bool swizzle128 = false);
 
 // Plan flags that select a schedule (the rest are options).
 constexpr unsigned kPathFlags = FFTSEG_FLAG_FORCE_TWOPASS | FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_PRODUCER |

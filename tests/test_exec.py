@@ -97,6 +97,25 @@ def test_persistent_fourstep_reuses_its_ring_many_times(variant):
     np.testing.assert_array_equal(run(plan, x), got)
 
 
+@pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
+def test_halfwarp_fourstep_65536_cycles_ring_in_place(direction, norm):
+    # n = 256 x 256 on the half-warp-line kernel: 32 segments per chunk, so 230
+    # segments cycle the 3-chunk ring more than twice and end in a partial chunk
+    n, B = 1 << 16, 230
+    x = siggen.tones(881, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2)
+    assert plan.info()["path"] == "four-step"
+    got = run(plan, x)
+    sample = np.r_[0:2, 95:98, B - 2:B]
+    assert rel_l2(got[sample], oracle.fft(x[sample], direction, norm)) <= tol_fp32(n)
+    np.testing.assert_array_equal(run(plan, x), got)  # the static schedule is deterministic
+    d = torch.from_numpy(x).cuda()
+    plan.exec(d, out=d)  # in place
+    torch.cuda.synchronize()
+    plan.check()
+    np.testing.assert_array_equal(d.cpu().numpy(), got)
+
+
 def test_persistent_fourstep_2p24_power():
     n = 1 << 24
     x = siggen.uniform(824, 2 * n).reshape(2, n)
