@@ -98,8 +98,8 @@ def test_persistent_fourstep_reuses_its_ring_many_times(variant):
 
 
 @pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
-def test_halfwarp_fourstep_65536_cycles_ring_in_place(direction, norm):
-    # n = 256 x 256 on the half-warp-line kernel: 32 segments per chunk, so 230
+def test_warp_line_fourstep_65536_cycles_ring_in_place(direction, norm):
+    # n = 256 x 256 on the warp-local-line kernel: 32 segments per chunk, so 230
     # segments cycle the 3-chunk ring more than twice and end in a partial chunk
     n, B = 1 << 16, 230
     x = siggen.tones(881, B * n).reshape(B, n)
