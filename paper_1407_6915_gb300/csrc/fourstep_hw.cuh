@@ -25,7 +25,7 @@
 //    base XORed with a compile-time constant, plus an immediate.
 //  - Two more warps per CTA do everything else over the CTA's static share of
 //    the work (items blockIdx.x, blockIdx.x + gridDim.x, ...), in order.  The
-//    loader waits for a free buffer (of three) and for the item's dependency,
+//    loader waits for a free buffer (of two) and for the item's dependency,
 //    then loads the tile (and, for column tiles, the tile's four-step twiddle
 //    factors) with TMA.  The retirer waits for the compute warps to finish an
 //    item, publishes finished tiles on their segment counters (a GPU-scope
@@ -50,15 +50,14 @@ struct FourStepHwArgs {
     CUtensorMap tmO;     // output [nseg][256][256], box [1][256][16], 128-byte swizzle
     float2 *ring;        // nr*cs segments, [slot*cs + sl][j2][k1]
     const float2 *twL;   // stage tables of a 256-point line (stage 1: [r-1][m], 240 entries)
-    const float2 *w4;    // [j2][16] = w_n^{j2 (k1 mod 16)}
-    const float2 *w4hi;  // [j2][16] = w_n^{j2 16 (k1 div 16)}
+    const float2 *w4t;   // per column tile ct: [16 cols][16] w_n^{j2 (k1 mod 16)}, then
+                         // [16 cols][16] scale * w_n^{j2 16 (k1 div 16)}
     int *ctr;            // per segment s < NC*cs: [1 + s] column tiles done, [1 + NC*cs + s] row tiles done
     int *err;
     int64_t nseg;
     int nchunks;         // NC
     int cs;              // segments per chunk
     int nr;              // ring buffers (at least FourStepHwShape::MIN_RING)
-    float scale;
 };
 
 struct FourStepHwShape {
@@ -66,20 +65,24 @@ struct FourStepHwShape {
     static constexpr int E = L * W;        // 4096 points per tile
     static constexpr int TC = 256;         // compute threads (8 warps, two lines each)
     static constexpr int TT = TC + 64;     // plus a loader warp and a retirer warp
-    static constexpr int NB = 3;           // tile buffers
+    // two tile buffers per CTA and three CTAs per SM (measured faster than
+    // three buffers and two CTAs: more compute warps for the same buffering)
+    static constexpr int NB = 2;           // tile buffers
+    static constexpr int MINB = 3;         // CTAs per SM (the registers must allow it)
     static constexpr int LOOKAHEAD = 1;    // column passes run this many chunks ahead of row passes
     static constexpr int MIN_RING = LOOKAHEAD + 2;
     static constexpr int TW = 240;         // stage-1 twiddles of a 256-point line
     static constexpr int FT = 2 * W * 16;  // a column tile's four-step factors: [16 cols][16], twice
     static constexpr int TILES_SEG = L / W;
     static constexpr uint32_t TILE_BYTES = E * sizeof(float2);
-    static constexpr uint32_t F_BYTES = W * 16 * sizeof(float2);  // one factor table of a tile
-    // P[NB] (1024-byte aligned) | F[NB] | stage table | full[NB], done[NB], empty[NB]
-    static constexpr size_t SMEM = (size_t)(NB * E + NB * FT + TW) * sizeof(float2) + 3 * NB * sizeof(uint64_t);
+    static constexpr uint32_t F_BYTES = FT * sizeof(float2);  // a column tile's factor tables
+    // P[NB] (1024-byte aligned) | F[NB] | stage table | full[NB], done[NB], empty[NB] | item[NB][4]
+    static constexpr size_t SMEM =
+        (size_t)(NB * E + NB * FT + TW) * sizeof(float2) + 3 * NB * sizeof(uint64_t) + NB * 4 * sizeof(int);
 };
 
 template <int S>
-__global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __grid_constant__ FourStepHwArgs a)
+__global__ void __launch_bounds__(FourStepHwShape::TT, FourStepHwShape::MINB) k_fourstep_hw(const __grid_constant__ FourStepHwArgs a)
 {
     using Sh = FourStepHwShape;
     constexpr int E = Sh::E, NB = Sh::NB, TC = Sh::TC, TSEG = Sh::TILES_SEG;
@@ -91,6 +94,7 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
     uint64_t *const full = reinterpret_cast<uint64_t *>(TWS + Sh::TW);
     uint64_t *const done = full + NB;
     uint64_t *const empty = done + NB;
+    int *const item = reinterpret_cast<int *>(empty + NB);  // [b]: row pass?, chunk, tile, segment (-1: none)
     const int tid = threadIdx.x;
     if (smem_u32(P) & 1023) {  // the swizzle pattern assumes 1024-byte aligned tiles
         if (tid == 0) atomicOr(a.err, 2);
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
     }
     if (tid >= TC) {
         // ============================================================== loader
-        // Loads this CTA's items in order into the three buffers once a buffer
+        // Loads this CTA's items in order into the tile buffers once a buffer
         // is free and the item's dependency is met (probed before the wait
         // for the buffer, so that the probe's latency overlaps it).
         const int lane = tid & 31;
@@ -245,17 +249,20 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
             }
             if (m >= NB) mbar_wait(&empty[b], (uint32_t)(m / NB - 1) & 1, a.err);
             if (lane == 0) {
+                // the decoded item, for the compute warps (released by the arrive below)
+                item[4 * b] = isb;
+                item[4 * b + 1] = c;
+                item[4 * b + 2] = w;
+                item[4 * b + 3] = s < a.nseg ? (int)s : -1;
                 if (s < a.nseg) {
                     if (isb) fence_proxy_async_global();  // ring data written by other CTAs' generic stores
                     fence_proxy_async();
                     float2 *dst = P + b * E;
                     if (!isb) {
                         const int ct = w % TSEG;
-                        mbar_expect_tx(&full[b], Sh::TILE_BYTES + 2 * Sh::F_BYTES);
+                        mbar_expect_tx(&full[b], Sh::TILE_BYTES + Sh::F_BYTES);
                         tma_load_3d_hint(dst, &a.tmA, ct * Sh::W, 0, (int)s, &full[b], stream_policy);
-                        float2 *f = F + b * Sh::FT;
-                        tma_load_1d(f, a.w4 + (int64_t)ct * Sh::W * 16, Sh::F_BYTES, &full[b]);
-                        tma_load_1d(f + Sh::W * 16, a.w4hi + (int64_t)ct * Sh::W * 16, Sh::F_BYTES, &full[b]);
+                        tma_load_1d(F + b * Sh::FT, a.w4t + (int64_t)ct * Sh::FT, Sh::F_BYTES, &full[b]);
                     } else {
                         const int slab = (c % a.nr) * a.cs + (int)(s - (int64_t)c * a.cs);
                         mbar_expect_tx(&full[b], Sh::TILE_BYTES);
@@ -287,15 +294,13 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
     const uint32_t wr = (uint32_t)(2048 * j + 8 * (h & 1)) + Mj;  // slot 16j + q: (wr ^ 144 (q mod 8)) + 1024 (q / 8)
     const uint32_t rd = (uint32_t)(1024 * (j >> 3) + 8 * (h & 1)) + Mj;  // slot j + 16r: (rd ^ 144 (r mod 8)) + 2048 r
     auto at = [&](uint32_t off) -> float2 & { return *reinterpret_cast<float2 *>(Pc + off); };
-    const float scale = a.scale;
 
+    int b = 0;
+    uint32_t par = 0;
     for (int64_t m = 0; m < items; ++m) {
-        const int b = (int)(m % NB);
-        int isb, c, w;
-        decode(first + m * stride, isb, c, w);
-        const int64_t s = (int64_t)c * a.cs + w / TSEG;
-        mbar_wait(&full[b], (uint32_t)(m / NB) & 1, a.err);
-        if (s < a.nseg) {
+        mbar_wait(&full[b], par, a.err);
+        const int isb = item[4 * b], c = item[4 * b + 1], w = item[4 * b + 2], s = item[4 * b + 3];
+        if (s >= 0) {
             const uint32_t tb = (uint32_t)b * Sh::TILE_BYTES;
             float2 v[16];
 #pragma unroll
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
             if (!isb) {
                 // column j2 = 16 ct + h: times w_n^{j2 k1} = w_n^{j2 j} w_n^{j2 16 q}, into the ring
                 const int ct = w % TSEG;
-                const int slab = (c % a.nr) * a.cs + (int)(s - (int64_t)c * a.cs);
+                const int slab = (c % a.nr) * a.cs + (s - c * a.cs);
                 const float2 *Fb = F + b * Sh::FT;
                 const float2 f1 = Fb[h * 16 + j];
                 float2 *dst = a.ring + (int64_t)slab * N + (int64_t)(ct * Sh::W + h) * Sh::L + j;
@@ -326,10 +331,7 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
             } else {
                 // row k1 = 16 rt + h: X[k1 + 256 k2], k2 = j + 16 q, staged as the
                 // output box [k2][k1 - 16 rt] in this line's own column of the tile
-                if (scale != 1.f) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q) v[q] = make_float2(v[q].x * scale, v[q].y * scale);
-                }
+                // (the plan's scale is already in the column pass's factors)
                 __syncwarp();  // every lane has read its exchange slots
 #pragma unroll
                 for (int q = 0; q < 16; ++q) at(tb + lin + 2048 * q) = v[q];
@@ -338,6 +340,10 @@ __global__ void __launch_bounds__(FourStepHwShape::TT, 2) k_fourstep_hw(const __
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&done[b]);
+        if (++b == NB) {
+            b = 0;
+            par ^= 1;
+        }
     }
 }
 

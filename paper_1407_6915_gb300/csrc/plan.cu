@@ -138,6 +138,7 @@ void free_plan(fftseg_plan p)
     cudaFree(p->ctr);
     cudaFree(p->w4);
     cudaFree(p->w4hi);
+    cudaFree(p->w4t);
     delete p;
 }
 
@@ -168,6 +169,19 @@ int build_fourstep(fftseg_plan p)
         std::vector<float2> h((size_t)(n2 * (n1 / K)));
         for (int64_t j2 = 0; j2 < n2; ++j2) host_roots(h.data() + j2 * (n1 / K), n1 / K, p->n, j2 * K);
         if ((rc = upload(&p->w4hi, h))) return rc;
+    }
+    if (uses_fourstep_hw(p)) {
+        // the same two factors grouped per column tile of 16 columns j2, the
+        // plan's scale (a power of two at n = 2^16, so exact) folded into the
+        // second: [ct][w_n^{j2 m}: 16 cols x 16][scale * w_n^{j2 16 q}: 16 cols x 16]
+        std::vector<float2> h((size_t)(n2 * 32));
+        for (int64_t j2 = 0; j2 < n2; ++j2) {
+            float2 *t = h.data() + (j2 >> 4) * 512 + (j2 & 15) * 16;
+            host_roots(t, 16, p->n, j2);
+            host_roots(t + 256, 16, p->n, j2 * 16);
+            for (int q = 0; q < 16; ++q) t[256 + q] = make_float2(t[256 + q].x * p->scale, t[256 + q].y * p->scale);
+        }
+        if ((rc = upload(&p->w4t, h))) return rc;
     }
     int64_t cs = kChunkBytes / (p->n * 8);
     if (cs < 1) cs = 1;
@@ -448,15 +462,13 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
                 a.ring = p->ring;
                 a.twL = p->twA;
-                a.w4 = p->w4;
-                a.w4hi = p->w4hi;
+                a.w4t = p->w4t;
                 a.ctr = p->ctr;
                 a.err = p->d_err;
                 a.nseg = nseg;
                 a.nchunks = (int)nc;
                 a.cs = p->ring_cs;
                 a.nr = p->ring_nr;
-                a.scale = p->scale;
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * p->ring_cs) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
                 e = launch_fourstep_hw(sign, a, st);

@@ -42,6 +42,7 @@ struct fftseg_plan_s {
     int *ctr = nullptr;       // queue head + per-chunk counters
     int64_t ctr_count = 0;
     float2 *w4 = nullptr, *w4hi = nullptr;
+    float2 *w4t = nullptr;  // the warp-local-line kernel's factors, per column tile (see fourstep_hw.cuh)
     int w4_log_k = 0;
     int log_wa = 0, log_wb = 0;
     // fftseg_stream phase split of the last call (ms)
