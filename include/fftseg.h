@@ -73,6 +73,18 @@ enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
 /* time every schedule built for n on the current GPU at plan creation and use
    the fastest (replaces the schedule flags above; see fftseg_autotune) */
 #define FFTSEG_FLAG_AUTOTUNE 0x10u
+/* real signal (the paper's records are real single-precision samples, Sec. III):
+   a forward plan of n points takes [batch][n] float32 samples and writes the
+   n/2 + 1 bins X[0..n/2] of each segment's DFT, [batch][n/2 + 1] complex64 (or
+   float32 |X|^2); an inverse plan takes [batch][n/2 + 1] complex64 bins and
+   writes [batch][n] float32 samples of the inverse DFT of their Hermitian
+   extension (the imaginary parts of X[0] and X[n/2] are ignored).  n is a power
+   of two in [4, 2^24]; FP32 only; out of place only; not for fftseg_stream,
+   fftseg_exec_host or the server.  Scaling as for complex plans, with n the
+   real length.  Runs as a complex FFT of n/2 points on the samples read as
+   complex values, plus one pass that splits (forward) or joins (inverse) the
+   spectra of the even and odd samples, in chunks whose intermediate stays in L2. */
+#define FFTSEG_FLAG_REAL 0x20u
 
 #define FFTSEG_MAX_LOG2N 24
 
@@ -180,7 +192,7 @@ int fftseg_exec_host(const fftseg_plan *plans, int nplans, const void *h_in, voi
 int fftseg_plan_destroy(fftseg_plan p);
 
 /* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core,
- * 4 persistent four-step),
+ * 4 persistent four-step, 5 real signal over an inner complex plan),
  * info[1] n1, info[2] n2, info[3] workspace bytes, info[4] segments per
  * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
 int fftseg_plan_info(fftseg_plan p, int64_t info[6]);

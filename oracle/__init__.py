@@ -78,3 +78,37 @@ def power(x, direction: int = FORWARD, norm: int = NORM_NONE, nthreads: int = No
     """|X|^2 of the segment-wise DFT, in double."""
     X = fft(x, direction, norm, nthreads)
     return X.real * X.real + X.imag * X.imag
+
+
+def rfft(x, norm: int = NORM_NONE, nthreads: int = None) -> np.ndarray:
+    """DFT of real segments, bins k = 0..n/2 (the paper's records are real
+    single-precision samples, Sec. III).
+
+    The definition written out: the complex DFT of the real samples (imaginary
+    part zero), forward, with the plan's scale (1, or 1/sqrt(n) for ORTHO),
+    keeping the first n/2 + 1 bins; the rest follow by X[n-k] = conj(X[k]).
+    ``x`` is float32 or float64, last axis of length n."""
+    x = np.asarray(x)
+    if x.dtype not in (np.float32, np.float64):
+        raise TypeError("oracle.rfft wants float32 or float64 input")
+    X = fft(x.astype(np.complex128), FORWARD, norm, nthreads)
+    return X[..., : x.shape[-1] // 2 + 1]
+
+
+def irfft(X, n: int, norm: int = NORM_NONE, nthreads: int = None) -> np.ndarray:
+    """Real signal of length n from the bins X[0..n/2] of its DFT.
+
+    The definition written out: the Hermitian extension Xf[k] = X[k] for
+    k <= n/2 and Xf[k] = conj(X[n-k]) above, with the imaginary parts of X[0]
+    and X[n/2] dropped (real bins of a real signal), through the inverse DFT
+    with the plan's scale (1, 1/n for BACKWARD, 1/sqrt(n) for ORTHO); the
+    result is real, its real part is returned."""
+    X = np.asarray(X, dtype=np.complex128)
+    if X.shape[-1] != n // 2 + 1:
+        raise ValueError("oracle.irfft wants n/2 + 1 bins")
+    Xf = np.empty(X.shape[:-1] + (n,), dtype=np.complex128)
+    Xf[..., : n // 2 + 1] = X
+    Xf[..., 0] = X[..., 0].real
+    Xf[..., n // 2] = X[..., n // 2].real
+    Xf[..., n // 2 + 1:] = np.conj(X[..., 1: n // 2][..., ::-1])
+    return fft(Xf, INVERSE, norm, nthreads).real

@@ -23,9 +23,10 @@ PREC_FP32, PREC_TC_FP16, PREC_TC_BF16 = 0, 1, 2
 OUT_COMPLEX, OUT_POWER = 0, 1
 FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2, FLAG_FOURSTEP_PRODUCER = 0x1, 0x2, 0x4, 0x8
 FLAG_AUTOTUNE = 0x10
+FLAG_REAL = 0x20
 
 
-PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step"}
+PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step", 5: "real"}
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_IO, E_PARTIAL, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 
@@ -193,17 +194,28 @@ class Plan:
         exec_host([self], h_in, h_out, self.batch if nseg is None else nseg, chunk_segments)
 
     def exec(self, x, out=None, nseg=None, stream=None):
-        """Transform the first nseg segments of the device tensor x (complex64,
-        contiguous, [.., n]); returns `out` (allocated if None)."""
+        """Transform the first nseg segments of the device tensor x; returns `out`
+        (allocated if None).  Complex plans: x complex64 [.., n].  Real-signal
+        plans (FLAG_REAL): forward x float32 [.., n] -> complex64 (or float32
+        power) [.., n/2 + 1]; inverse x complex64 [.., n/2 + 1] -> float32 [.., n]."""
         import torch
         if not (x.is_cuda and x.is_contiguous()):
             raise ValueError("fftseg.Plan.exec wants a contiguous CUDA tensor")
-        if x.dtype != torch.complex64:
-            raise ValueError("fftseg.Plan.exec wants complex64 input")
-        nseg = (x.numel() // self.n) if nseg is None else nseg
+        real = bool(self.flags & FLAG_REAL)
+        if real and self.direction == FORWARD:
+            want, seg_in, seg_out = torch.float32, self.n, self.n // 2 + 1
+            out_dt = torch.float32 if self.out_kind == OUT_POWER else torch.complex64
+        elif real:
+            want, seg_in, seg_out, out_dt = torch.complex64, self.n // 2 + 1, self.n, torch.float32
+        else:
+            want, seg_in, seg_out = torch.complex64, self.n, self.n
+            out_dt = torch.float32 if self.out_kind == OUT_POWER else torch.complex64
+        if x.dtype != want:
+            raise ValueError("fftseg.Plan.exec wants %s input for this plan" % want)
+        nseg = (x.numel() // seg_in) if nseg is None else nseg
         if out is None:
-            dt = torch.float32 if self.out_kind == OUT_POWER else torch.complex64
-            out = torch.empty(x.shape, dtype=dt, device=x.device)
+            shape = tuple(x.shape[:-1]) + (seg_out,) if x.dim() > 1 else (x.numel() // seg_in * seg_out,)
+            out = torch.empty(shape, dtype=out_dt, device=x.device)
         self.exec_ptr(x.data_ptr(), out.data_ptr(), nseg, stream)
         return out
 

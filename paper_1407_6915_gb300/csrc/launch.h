@@ -38,6 +38,20 @@ cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cud
 // output): producer warp, three swizzled TMA tile buffers, TMA output stores.
 struct FourStepHwArgs;
 cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t st);
+// Real-signal segments (k_real.cu): the pass between a length-n real DFT and
+// the length-m = n/2 complex DFT.  post: complex FFT output [nseg][m] -> the
+// n/2 + 1 bins [nseg][m + 1] (complex64, or float32 |X|^2 with power); pre:
+// bins [nseg][m + 1] -> complex FFT input [nseg][m].  Both apply `scale`.
+struct RealArgs {
+    const float2 *zin;  // post: [nseg][m]
+    const float2 *xin;  // pre: [nseg][m + 1]
+    void *out;
+    const float2 *tw;   // w_n^k, k = 0 .. m/2 (forward values)
+    int64_t blocks_per_seg;  // set by launch_real
+    int m;
+    float scale;
+};
+cudaError_t launch_real(bool post, bool power, RealArgs a, int64_t nseg, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

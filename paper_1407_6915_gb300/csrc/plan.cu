@@ -127,6 +127,9 @@ int fourstep_table(float2 **dst, int64_t n, int64_t rows, int64_t row_mult, int6
 void free_plan(fftseg_plan p)
 {
     if (!p) return;
+    free_plan(p->inner);
+    cudaFree(p->rtw);
+    cudaFree(p->rwork);
     if (p->host_stage && p->host_stage_free) p->host_stage_free(p->host_stage);
     cudaFree(p->twA);
     cudaFree(p->twB);
@@ -286,6 +289,12 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
+        case PATH_REAL: {
+            int64_t k = 0;
+            for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
+                k += 1 + launches_per_exec(p->inner, nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk);
+            return k;
+        }
         default: return 0;
     }
 }
@@ -322,6 +331,38 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
+    if (p->path == PATH_REAL) {
+        // chunks of rchunk segments: the complex FFT of n/2 points and the
+        // split (forward) or join (inverse) pass, through an L2-sized intermediate
+        const int64_t M = p->n / 2;
+        const bool power = p->out_kind == FFTSEG_OUT_POWER;
+        for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
+            const int64_t cnt = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
+            RealArgs a{};
+            a.m = (int)M;
+            a.tw = p->rtw;
+            a.scale = p->scale;
+            int rc;
+            if (p->direction == FFTSEG_FORWARD) {
+                rc = exec_plan(p->inner, static_cast<const float2 *>(d_in) + s0 * M, p->rwork, cnt, st);
+                if (rc != FFTSEG_OK) return rc;
+                a.zin = p->rwork;
+                a.out = static_cast<char *>(d_out) + s0 * (M + 1) * (power ? 4 : 8);
+                cudaError_t e = launch_real(true, power, a, cnt, st);
+                if (e != cudaSuccess) return cuda_error(e, "real-signal split launch");
+                count_launches(1);
+            } else {
+                a.xin = static_cast<const float2 *>(d_in) + s0 * (M + 1);
+                a.out = p->rwork;
+                cudaError_t e = launch_real(false, false, a, cnt, st);
+                if (e != cudaSuccess) return cuda_error(e, "real-signal join launch");
+                count_launches(1);
+                rc = exec_plan(p->inner, p->rwork, static_cast<float2 *>(d_out) + s0 * M, cnt, st);
+                if (rc != FFTSEG_OK) return rc;
+            }
+        }
+        return FFTSEG_OK;
+    }
     if (nseg == 0) return FFTSEG_OK;
     const float2 *in = static_cast<const float2 *>(d_in);
     const int sign = p->direction;
@@ -511,6 +552,64 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
     }
 }
 
+// Real-signal plan: a complex plan of n/2 points (its schedule flags, and an
+// autotune request, go to it), the split/join twiddles w_n^k (k <= n/4) and an
+// intermediate of kRealChunkBytes that stays in L2 between the two passes.
+constexpr int64_t kRealChunkBytes = 32ll << 20;
+
+int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int precision, int out_kind,
+                unsigned flags)
+{
+    if (n < 4) return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: real-signal plans need n >= 4");
+    if (precision != FFTSEG_PREC_FP32)
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: real-signal plans are FP32 only");
+    if (direction == FFTSEG_INVERSE && out_kind == FFTSEG_OUT_POWER)
+        return set_error(FFTSEG_E_INVALID, "plan_create: the power output belongs to forward real-signal plans");
+    fftseg_plan p = new (std::nothrow) fftseg_plan_s();
+    if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    p->n = n;
+    p->batch = batch;
+    p->log_n = ilog2(n);
+    p->direction = direction;
+    p->norm = norm;
+    p->precision = precision;
+    p->out_kind = out_kind;
+    p->flags = flags;
+    p->path = PATH_REAL;
+    if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
+    else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
+    const int64_t M = n / 2;
+    p->log_n1 = ilog2(M);
+    int64_t cs = kRealChunkBytes / (M * 8);
+    if (cs < 1) cs = 1;
+    if (cs > batch) cs = batch;
+    p->rchunk = cs;
+    int rc = fftseg_plan_create(&p->inner, M, cs, direction, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
+                                FFTSEG_OUT_COMPLEX, flags & ~FFTSEG_FLAG_REAL);
+    if (rc == FFTSEG_OK) {
+        std::vector<float2> h((size_t)(M / 2 + 1));
+        host_roots(h.data(), M / 2 + 1, n, 1);
+        rc = upload(&p->rtw, h);
+    }
+    if (rc == FFTSEG_OK) {
+        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(real-signal intermediate)");
+    }
+    if (rc != FFTSEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FFTSEG_OK;
+}
+
 }  // namespace fftseg
 
 using namespace fftseg;
@@ -536,6 +635,7 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
         return set_error(FFTSEG_E_INVALID, "plan_create: bad precision %d", precision);
     if (batch > (int64_t(1) << 40) / n)
         return set_error(FFTSEG_E_INVALID, "plan_create: batch*n too large");
+    if (flags & FFTSEG_FLAG_REAL) return create_real(out, n, batch, direction, norm, precision, out_kind, flags);
     if (flags & FFTSEG_FLAG_AUTOTUNE) {  // replace the schedule flags by the fastest measured schedule
         unsigned chosen = 0;
         const int trc = tune_schedule(n, batch, precision, out_kind, &chosen, nullptr);
@@ -594,6 +694,8 @@ int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, ff
         return set_error(FFTSEG_E_INVALID, "exec: buffers must be 16-byte aligned");
     if (d_in == d_out && p->out_kind == FFTSEG_OUT_POWER)
         return set_error(FFTSEG_E_INVALID, "exec: the power output cannot be written in place");
+    if (d_in == d_out && p->path == PATH_REAL)
+        return set_error(FFTSEG_E_INVALID, "exec: real-signal plans work out of place only");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -614,9 +716,11 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
     if (!p || !info) return set_error(FFTSEG_E_INVALID, "plan_info: NULL argument");
     info[0] = p->path;
     info[1] = int64_t(1) << p->log_n1;
-    info[2] = p->path == PATH_BLOCK ? 1 : int64_t(1) << p->log_n2;
-    info[3] = p->work ? p->work_segs * p->n * 8 : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
-    info[4] = p->work ? p->work_segs : p->ring_cs;
+    info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL) ? 1 : int64_t(1) << p->log_n2;
+    info[3] = p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
+                                    : p->work ? p->work_segs * p->n * 8
+                                              : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
+    info[4] = p->path == PATH_REAL ? p->rchunk : p->work ? p->work_segs : p->ring_cs;
     info[5] = launches_per_exec(p, p->batch);
     return FFTSEG_OK;
 }
@@ -624,6 +728,10 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
 int fftseg_plan_check(fftseg_plan p)
 {
     if (!p) return set_error(FFTSEG_E_INVALID, "plan_check: NULL plan");
+    if (p->inner) {
+        const int rc = fftseg_plan_check(p->inner);
+        if (rc != FFTSEG_OK) return rc;
+    }
     int flag = 0;
     cudaError_t e = cudaMemcpy(&flag, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_error(e, "plan_check");

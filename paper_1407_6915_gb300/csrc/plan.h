@@ -12,7 +12,7 @@
 
 namespace fftseg {
 
-enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4 };
+enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4, PATH_REAL = 5 };
 
 }  // namespace fftseg
 
@@ -45,6 +45,11 @@ struct fftseg_plan_s {
     float2 *w4t = nullptr;  // the warp-local-line kernel's factors, per column tile (see fourstep_hw.cuh)
     int w4_log_k = 0;
     int log_wa = 0, log_wb = 0;
+    // real-signal plans (FFTSEG_FLAG_REAL): a complex plan of n/2 points
+    fftseg_plan_s *inner = nullptr;
+    float2 *rtw = nullptr;    // w_n^k, k = 0 .. n/4
+    float2 *rwork = nullptr;  // [rchunk][n/2] complex intermediate
+    int64_t rchunk = 0;
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
     // fftseg_exec_host device staging (owned; released with the plan)

@@ -247,3 +247,34 @@ def test_planted_mistakes_are_caught(tmp_path, name):
         if rel_l2(out, brute_dft(x, direction, scale)) > 1e-6:
             caught = True
     assert caught, "mutation %s survived the brute-force pin" % name
+
+
+# ---- real-signal segments (rfft / irfft): pinned against the complex DFT's
+# symmetry, a library cross-check and the round trip
+
+@pytest.mark.parametrize("n", [4, 8, 16, 256, 4096])
+def test_rfft_is_the_half_spectrum_of_the_brute_force_dft(n):
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((3, n))
+    X = oracle.rfft(x)
+    ref = brute_dft(x.astype(np.complex128), -1, 1.0)[:, : n // 2 + 1]
+    assert rel_l2(X, ref) < 1e-12
+    assert np.all(np.abs(X[:, 0].imag) < 1e-9) and np.all(np.abs(X[:, n // 2].imag) < 1e-9)
+
+
+@pytest.mark.parametrize("n", [4, 64, 1 << 14])
+@pytest.mark.parametrize("norm,np_norm", [(NONE, "backward"), (ORTHO, "ortho")])
+def test_rfft_irfft_match_numpy(n, norm, np_norm):
+    rng = np.random.default_rng(7 + n)
+    x = rng.standard_normal((2, n))
+    assert rel_l2(oracle.rfft(x, norm), np.fft.rfft(x, norm=np_norm)) < 1e-12
+    X = np.fft.rfft(x) + 1j * 0.25  # the imaginary parts of X[0], X[n/2] must be ignored
+    want = np.fft.irfft(X, n, norm="forward" if norm == NONE else "ortho")
+    assert rel_l2(oracle.irfft(X, n, norm), want) < 1e-12
+
+
+@pytest.mark.parametrize("n", [4, 32, 1 << 12])
+def test_irfft_inverts_rfft(n):
+    x = np.random.default_rng(n).standard_normal((4, n))
+    assert rel_l2(oracle.irfft(oracle.rfft(x), n, BACK), x) < 1e-12
+    assert rel_l2(oracle.irfft(oracle.rfft(x, ORTHO), n, ORTHO), x) < 1e-12

@@ -1,0 +1,117 @@
+"""Real-signal segments (FFTSEG_FLAG_REAL) against the FP64 oracle.
+
+The paper's records are real single-precision samples (Sec. III: a 1024-point
+record is 4096 bytes).  A forward real plan writes the n/2 + 1 bins of each
+segment's DFT; an inverse plan goes back from those bins.  Sizes span the
+block, cluster and four-step paths of the inner n/2-point transform, batches
+span several chunks of the intermediate with a ragged last chunk.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from tests._util import rel_l2, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1407_6915_gb300 as fs  # noqa: E402
+
+FWD, INV = fs.FORWARD, fs.INVERSE
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_6915_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def real_signal(seed, nseg, n):
+    # the real and imaginary parts of a tones + noise signal, as 2*nseg*n/2 reals
+    return siggen.tones(seed, nseg * n // 2).view(np.float32).reshape(nseg, n)
+
+
+def nseg_for(n):
+    # more than one 32 MiB chunk of the n/2-point intermediate, plus a ragged tail
+    return max(3, (48 << 20) // (4 * n) + 1) if n <= (1 << 20) else 3
+
+
+@pytest.mark.parametrize("log_n", [2, 3, 4, 5, 8, 10, 12, 13, 14, 16, 17, 20])
+@pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_ORTHO])
+def test_r2c_matches_oracle(log_n, norm):
+    n = 1 << log_n
+    B = nseg_for(n)
+    x = real_signal(100 + log_n, B, n)
+    plan = fs.Plan(n, B, FWD, norm, flags=fs.FLAG_REAL)
+    assert plan.info()["path"] == "real"
+    got = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    assert got.shape == (B, n // 2 + 1)
+    got = got.cpu().numpy().astype(np.complex128)
+    sample = np.r_[0:2, B // 2, B - 1]
+    ref = oracle.rfft(x[sample], norm)
+    assert rel_l2(got[sample], ref) <= tol_fp32(n)
+    # real bins are real
+    assert np.all(got[:, 0].imag == 0) and np.all(got[:, n // 2].imag == 0)
+
+
+@pytest.mark.parametrize("log_n", [2, 4, 9, 12, 15, 16, 18])
+def test_r2c_power(log_n):
+    n = 1 << log_n
+    B = 5
+    x = real_signal(300 + log_n, B, n)
+    plan = fs.Plan(n, B, FWD, out_kind=fs.OUT_POWER, flags=fs.FLAG_REAL)
+    got = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    X = oracle.rfft(x)
+    assert rel_l2(got.cpu().numpy(), X.real ** 2 + X.imag ** 2) <= 2 * tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n", [2, 3, 6, 12, 13, 16, 20])
+@pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_BACKWARD, fs.NORM_ORTHO])
+def test_c2r_matches_oracle(log_n, norm):
+    n = 1 << log_n
+    B = nseg_for(n)
+    X = oracle.rfft(real_signal(500 + log_n, B, n)).astype(np.complex64)
+    X[:, 0] += 0.5j  # the imaginary parts of the real bins are ignored
+    X[:, n // 2] -= 0.25j
+    plan = fs.Plan(n, B, INV, norm, flags=fs.FLAG_REAL)
+    got = plan.exec(torch.from_numpy(X).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    assert got.shape == (B, n) and got.dtype == torch.float32
+    got = got.cpu().numpy()
+    sample = np.r_[0:2, B // 2, B - 1]
+    ref = oracle.irfft(X[sample], n, norm)
+    assert rel_l2(got[sample], ref) <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n", [2, 10, 16, 17])
+def test_round_trip(log_n):
+    n = 1 << log_n
+    B = 7
+    x = real_signal(700 + log_n, B, n)
+    fwd = fs.Plan(n, B, FWD, flags=fs.FLAG_REAL)
+    inv = fs.Plan(n, B, INV, fs.NORM_BACKWARD, flags=fs.FLAG_REAL)
+    y = inv.exec(fwd.exec(torch.from_numpy(x).cuda()))
+    torch.cuda.synchronize()
+    assert rel_l2(y.cpu().numpy(), x) <= 2 * tol_fp32(n)
+
+
+def test_real_plan_rejections():
+    with pytest.raises(fs.FFTSegError):
+        fs.Plan(2, 1, FWD, flags=fs.FLAG_REAL)  # n >= 4
+    with pytest.raises(fs.FFTSegError):
+        fs.Plan(1 << 12, 1, FWD, precision=fs.PREC_TC_FP16, flags=fs.FLAG_REAL)  # FP32 only
+    with pytest.raises(fs.FFTSegError):
+        fs.Plan(1 << 12, 1, INV, out_kind=fs.OUT_POWER, flags=fs.FLAG_REAL)
+    plan = fs.Plan(1 << 12, 2, FWD, flags=fs.FLAG_REAL)
+    buf = torch.zeros(2 << 12, dtype=torch.float32, device="cuda")
+    with pytest.raises(fs.FFTSegError):
+        plan.exec_ptr(buf.data_ptr(), buf.data_ptr())  # out of place only
+    with pytest.raises(fs.FFTSegError):
+        plan.exec_host(torch.zeros(2 << 12), torch.zeros(2 << 12))
