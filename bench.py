@@ -377,6 +377,51 @@ def real_bench(peak):
             "flops_convention": "2.5 n log2 n per real segment", "sizes": rows}
 
 
+def frames_bench(peak):
+    """Overlapping segments (FramePlan): a 2^29-sample complex64 signal (4 GiB),
+    periodic Hann window, hop n/2, at n = 1024 and 65536.  Algorithmic bytes per
+    frame: 8 hop read (each sample once, overlaps re-read from L2) + 8 n written."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    count = 1 << 29
+    h = torch.empty(count, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_TONES, 7, 0, count, h.data_ptr())
+    x = h.cuda()
+    rows = []
+    for n in (1024, 65536):
+        hop = n // 2
+        plan = fs.FramePlan(n, hop, (count - n) // hop + 1, fs.WINDOW_HANN)
+        F = plan.frames_in(count)
+        y = torch.empty(F, n, dtype=torch.complex64, device="cuda")
+        for _ in range(3):
+            plan.exec(x, out=y)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(5):
+            plan.exec(x, out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        ms = e0.elapsed_time(e1) / 5
+        algo = F * (8.0 * hop + 8.0 * n)
+        ref = oracle.frames_fft(x[: hop + n].cpu().numpy(), n, hop, 2, oracle.WINDOW_HANN)
+        err = float(np.linalg.norm(y[:2].cpu().numpy().astype(np.complex128) - ref) / np.linalg.norm(ref))
+        rows.append({"n": n, "hop": hop, "frames": F, "ms": round(ms, 4),
+                     "gflops": round(5.0 * n * math.log2(n) * F / (ms / 1e3) / 1e9, 1),
+                     "gbs_algorithmic": round(algo / (ms / 1e3) / 1e9, 1),
+                     "hbm_frac": round(algo / (ms / 1e3) / 1e9 / peak, 4),
+                     "rel_l2_first_2_frames": err})
+        del y, plan
+        torch.cuda.empty_cache()
+    del x, h
+    torch.cuda.empty_cache()
+    return {"what": "short-time FFT: Hann-windowed frames of a tones + noise signal (seed 7), hop n/2",
+            "sizes": rows}
+
+
 def tune_table():
     """The autotuner's choice per length (FP32, complex output, a 256 MiB batch)
     beside the library's default schedule."""
@@ -660,6 +705,7 @@ def run_ours(args):
             line["stream"] = stream_bench(link, h_in)
             line["tc_split"] = tc_split(peak)
             line["real"] = real_bench(peak)
+            line["frames"] = frames_bench(peak)
             line["autotune"] = tune_table()
             line["serve"] = serve_bench(peak)
     if world > 1:

@@ -60,6 +60,7 @@ enum { FFTSEG_FORWARD = -1, FFTSEG_INVERSE = +1 };
 enum { FFTSEG_NORM_NONE = 0, FFTSEG_NORM_BACKWARD = 1, FFTSEG_NORM_ORTHO = 2 };
 enum { FFTSEG_PREC_FP32 = 0, FFTSEG_PREC_TC_FP16 = 1, FFTSEG_PREC_TC_BF16 = 2 };
 enum { FFTSEG_OUT_COMPLEX = 0, FFTSEG_OUT_POWER = 1 };
+enum { FFTSEG_WINDOW_RECT = 0, FFTSEG_WINDOW_HANN = 1 };
 
 /* plan flags */
 #define FFTSEG_FLAG_ZERO_PAD 0x1u     /* fftseg_stream: zero-pad a trailing partial segment */
@@ -118,6 +119,31 @@ int fftseg_exec(fftseg_plan p, const void *d_in, void *d_out, fftseg_stream_t st
 /* As fftseg_exec for the first `nseg` (0 <= nseg <= batch) segments. */
 int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg,
                   fftseg_stream_t stream);
+
+/*
+ * Overlapping segments, a short-time FFT (the paper names overlapping FFTs as
+ * future work, Sec. VI): frame f of the signal holds samples [f*hop, f*hop + n),
+ * multiplied point by point by the window, and is transformed like a segment
+ * of a forward complex plan:
+ *     X_f[k] = scale * sum_{j<n} w[j] x[f*hop + j] exp(-2 pi i j k / n)
+ *   n        power of two, 2 <= n <= 2^24, else FFTSEG_E_UNSUPPORTED
+ *   hop      >= 1 samples between frame starts (hop < n overlaps, hop > n skips)
+ *   window   FFTSEG_WINDOW_RECT (w = 1) or FFTSEG_WINDOW_HANN
+ *            (w[j] = (1 - cos(2 pi j / n)) / 2, the periodic Hann window,
+ *            evaluated in double and rounded once to float32)
+ *   batch    >= 1: the most frames one exec processes
+ *   norm, out_kind, flags  as for fftseg_plan_create (schedule flags and
+ *            FFTSEG_FLAG_AUTOTUNE apply to the n-point transform; FFTSEG_FLAG_REAL
+ *            is not built for frames)
+ * Run it with fftseg_exec / fftseg_exec_n: d_in is the complex64 signal and must
+ * hold at least (nframes - 1)*hop + n samples (the library cannot check the
+ * size of a device buffer); d_out is [nframes][n] complex64 (or float32 |X|^2);
+ * out of place only.  Frames are windowed into an intermediate of at most
+ * 32 MiB, which then goes through the n-point transform.  Not for fftseg_stream,
+ * fftseg_exec_host or the server.
+ */
+int fftseg_plan_create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t batch, int norm,
+                              int out_kind, unsigned flags);
 
 /*
  * Streaming chunker (Sec. III's split/transform/merge on one GPU; the paper's
@@ -192,7 +218,8 @@ int fftseg_exec_host(const fftseg_plan *plans, int nplans, const void *h_in, voi
 int fftseg_plan_destroy(fftseg_plan p);
 
 /* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core,
- * 4 persistent four-step, 5 real signal over an inner complex plan),
+ * 4 persistent four-step, 5 real signal over an inner complex plan,
+ * 6 overlapping frames over an inner complex plan),
  * info[1] n1, info[2] n2, info[3] workspace bytes, info[4] segments per
  * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
 int fftseg_plan_info(fftseg_plan p, int64_t info[6]);

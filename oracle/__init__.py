@@ -112,3 +112,27 @@ def irfft(X, n: int, norm: int = NORM_NONE, nthreads: int = None) -> np.ndarray:
     Xf[..., n // 2] = X[..., n // 2].real
     Xf[..., n // 2 + 1:] = np.conj(X[..., 1: n // 2][..., ::-1])
     return fft(Xf, INVERSE, norm, nthreads).real
+
+
+WINDOW_RECT, WINDOW_HANN = 0, 1
+
+
+def window(n: int, kind: int) -> np.ndarray:
+    """The frame window in double: 1 (rectangular) or the periodic Hann window
+    w[j] = (1 - cos(2 pi j / n)) / 2."""
+    if kind == WINDOW_RECT:
+        return np.ones(n)
+    if kind == WINDOW_HANN:
+        return 0.5 - 0.5 * np.cos(2.0 * np.pi * np.arange(n) / n)
+    raise ValueError("unknown window %r" % kind)
+
+
+def frames_fft(x, n: int, hop: int, nframes: int, kind: int = WINDOW_HANN, norm: int = NORM_NONE,
+               nthreads: int = None) -> np.ndarray:
+    """Overlapping segments, the definition written out: frame f holds samples
+    x[f*hop .. f*hop + n - 1] (x complex, one signal), times the window, then
+    the forward DFT with the plan's scale.  Returns [nframes][n] complex128."""
+    x = np.asarray(x)
+    idx = np.arange(nframes)[:, None] * hop + np.arange(n)[None, :]
+    fr = x.astype(np.complex128)[idx] * window(n, kind)[None, :]
+    return fft(fr, FORWARD, norm, nthreads)

@@ -26,7 +26,9 @@ FLAG_AUTOTUNE = 0x10
 FLAG_REAL = 0x20
 
 
-PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step", 5: "real"}
+WINDOW_RECT, WINDOW_HANN = 0, 1
+PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step", 5: "real",
+              6: "frames"}
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_IO, E_PARTIAL, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 
@@ -64,6 +66,9 @@ _lib = None
 _SIGS = {
     "fftseg_plan_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint]),
+    "fftseg_plan_create_frames": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64, ctypes.c_int64,
+                                                 ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_uint]),
     "fftseg_exec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "fftseg_exec_n": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                      ctypes.c_void_p]),
@@ -259,6 +264,41 @@ class Plan:
             self.destroy()
         except Exception:
             pass
+
+
+class FramePlan(Plan):
+    """Overlapping segments, a short-time FFT (fftseg_plan_create_frames): frame
+    f of the signal holds samples [f*hop, f*hop + n), multiplied by the window,
+    and is transformed forward like a segment of a complex plan."""
+
+    def __init__(self, n, hop, batch, window=WINDOW_HANN, norm=NORM_NONE, out_kind=OUT_COMPLEX, flags=0):
+        self._h = ctypes.c_void_p()
+        self.n, self.batch, self.direction, self.norm = int(n), int(batch), FORWARD, norm
+        self.precision, self.out_kind, self.flags = PREC_FP32, out_kind, flags
+        self.hop, self.window = int(hop), window
+        check(lib().fftseg_plan_create_frames(ctypes.byref(self._h), self.n, self.hop, window, self.batch, norm,
+                                              out_kind, flags), "fftseg_plan_create_frames")
+
+    def frames_in(self, samples: int) -> int:
+        """Whole frames in a signal of `samples` samples."""
+        return 0 if samples < self.n else (samples - self.n) // self.hop + 1
+
+    def exec(self, x, out=None, nseg=None, stream=None):
+        """Frames of the complex64 device signal x (contiguous): the first
+        nseg frames (default: every whole frame, at most batch) -> out
+        [nframes][n] (complex64, or float32 |X|^2)."""
+        import torch
+        if not (x.is_cuda and x.is_contiguous() and x.dtype == torch.complex64):
+            raise ValueError("fftseg.FramePlan.exec wants a contiguous complex64 CUDA tensor")
+        avail = self.frames_in(x.numel())
+        nf = min(avail, self.batch) if nseg is None else int(nseg)
+        if nf > avail:
+            raise ValueError("the signal holds %d whole frames, %d asked" % (avail, nf))
+        if out is None:
+            dt = torch.float32 if self.out_kind == OUT_POWER else torch.complex64
+            out = torch.empty((nf, self.n), dtype=dt, device=x.device)
+        self.exec_ptr(x.data_ptr(), out.data_ptr(), nf, stream)
+        return out
 
 
 class Server:

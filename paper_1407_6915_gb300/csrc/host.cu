@@ -79,8 +79,8 @@ extern "C" int fftseg_exec_host(const fftseg_plan *plans, int nplans, const void
     for (int k = 0; k < nplans; ++k) {
         const fftseg_plan p = plans[k];
         if (p->n != n) return set_error(FFTSEG_E_INVALID, "exec_host: plans of different lengths");
-        if (p->path == PATH_REAL)
-            return set_error(FFTSEG_E_UNSUPPORTED, "exec_host: real-signal plans are not supported here");
+        if (p->path == PATH_REAL || p->path == PATH_FRAMES)
+            return set_error(FFTSEG_E_UNSUPPORTED, "exec_host: real-signal and frame plans are not supported here");
         if (p->device != p0->device) return set_error(FFTSEG_E_INVALID, "exec_host: plans on different devices");
         if (k + 1 < nplans && p->out_kind != FFTSEG_OUT_COMPLEX)
             return set_error(FFTSEG_E_INVALID, "exec_host: only the last plan may write the power output");

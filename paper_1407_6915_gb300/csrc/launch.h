@@ -52,6 +52,17 @@ struct RealArgs {
     float scale;
 };
 cudaError_t launch_real(bool post, bool power, RealArgs a, int64_t nseg, cudaStream_t st);
+// Overlapping segments (frames.cu): windowed frames f = samples
+// [f*hop, f*hop + n) of the signal into [nframes][n] complex64.
+struct FramesArgs {
+    const float2 *signal;
+    float2 *frames;
+    const float *window;  // n values, or null for the rectangular window
+    int64_t hop;
+    int64_t blocks_per_frame;  // set by launch_frames
+    int n;
+};
+cudaError_t launch_frames(FramesArgs a, int64_t nframes, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

@@ -130,6 +130,7 @@ void free_plan(fftseg_plan p)
     free_plan(p->inner);
     cudaFree(p->rtw);
     cudaFree(p->rwork);
+    cudaFree(p->fwin);
     if (p->host_stage && p->host_stage_free) p->host_stage_free(p->host_stage);
     cudaFree(p->twA);
     cudaFree(p->twB);
@@ -289,7 +290,8 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
-        case PATH_REAL: {
+        case PATH_REAL:
+        case PATH_FRAMES: {
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
                 k += 1 + launches_per_exec(p->inner, nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk);
@@ -331,6 +333,27 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
+    if (p->path == PATH_FRAMES) {
+        // chunks of rchunk frames: windowed frames into an L2-sized
+        // intermediate, then the batched complex plan of n points
+        const bool power = p->out_kind == FFTSEG_OUT_POWER;
+        for (int64_t f0 = 0; f0 < nseg; f0 += p->rchunk) {
+            const int64_t cnt = nseg - f0 < p->rchunk ? nseg - f0 : p->rchunk;
+            FramesArgs a{};
+            a.signal = static_cast<const float2 *>(d_in) + f0 * p->hop;
+            a.frames = p->rwork;
+            a.window = p->fwin;
+            a.hop = p->hop;
+            a.n = (int)p->n;
+            cudaError_t e = launch_frames(a, cnt, st);
+            if (e != cudaSuccess) return cuda_error(e, "frames launch");
+            count_launches(1);
+            const int rc = exec_plan(p->inner, p->rwork, static_cast<char *>(d_out) + f0 * p->n * (power ? 4 : 8),
+                                     cnt, st);
+            if (rc != FFTSEG_OK) return rc;
+        }
+        return FFTSEG_OK;
+    }
     if (p->path == PATH_REAL) {
         // chunks of rchunk segments: the complex FFT of n/2 points and the
         // split (forward) or join (inverse) pass, through an L2-sized intermediate
@@ -610,6 +633,58 @@ int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int n
     return FFTSEG_OK;
 }
 
+// Overlapping-segment plan: a forward complex plan of n points over a chunk
+// of windowed frames (its schedule flags, and an autotune request, go to it).
+int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t batch, int norm, int out_kind,
+                  unsigned flags)
+{
+    fftseg_plan p = new (std::nothrow) fftseg_plan_s();
+    if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create_frames: host allocation failed");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    p->n = n;
+    p->batch = batch;
+    p->log_n = ilog2(n);
+    p->log_n1 = p->log_n;
+    p->direction = FFTSEG_FORWARD;
+    p->norm = norm;
+    p->precision = FFTSEG_PREC_FP32;
+    p->out_kind = out_kind;
+    p->flags = flags;
+    p->path = PATH_FRAMES;
+    p->hop = hop;
+    p->window = window;
+    int64_t cs = kRealChunkBytes / (n * 8);
+    if (cs < 1) cs = 1;
+    if (cs > batch) cs = batch;
+    p->rchunk = cs;
+    int rc = fftseg_plan_create(&p->inner, n, cs, FFTSEG_FORWARD, norm, FFTSEG_PREC_FP32, out_kind, flags);
+    if (rc == FFTSEG_OK && window == FFTSEG_WINDOW_HANN) {
+        // periodic Hann window, w[j] = (1 - cos(2 pi j / n)) / 2, evaluated in double
+        std::vector<float> h((size_t)n);
+        const double two_pi = 6.283185307179586476925286766559;
+        for (int64_t j = 0; j < n; ++j) h[(size_t)j] = (float)(0.5 - 0.5 * cos(two_pi * (double)j / (double)n));
+        e = cudaMalloc((void **)&p->fwin, (size_t)n * sizeof(float));
+        if (e == cudaSuccess) e = cudaMemcpy(p->fwin, h.data(), (size_t)n * sizeof(float), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) rc = cuda_error(e, "window table");
+    }
+    if (rc == FFTSEG_OK) {
+        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * n) * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(frames intermediate)");
+    }
+    if (rc != FFTSEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FFTSEG_OK;
+}
+
 }  // namespace fftseg
 
 using namespace fftseg;
@@ -675,6 +750,29 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
     return FFTSEG_OK;
 }
 
+int fftseg_plan_create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t batch, int norm,
+                              int out_kind, unsigned flags)
+{
+    if (!out) return set_error(FFTSEG_E_INVALID, "plan_create_frames: out is NULL");
+    *out = nullptr;
+    if (!is_pow2(n) || n < 2 || n > (int64_t(1) << FFTSEG_MAX_LOG2N))
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create_frames: n=%lld is not a power of two in [2, 2^24]",
+                         (long long)n);
+    if (hop < 1) return set_error(FFTSEG_E_INVALID, "plan_create_frames: hop must be >= 1");
+    if (window != FFTSEG_WINDOW_RECT && window != FFTSEG_WINDOW_HANN)
+        return set_error(FFTSEG_E_INVALID, "plan_create_frames: bad window %d", window);
+    if (batch < 1) return set_error(FFTSEG_E_INVALID, "plan_create_frames: batch must be >= 1");
+    if (norm < FFTSEG_NORM_NONE || norm > FFTSEG_NORM_ORTHO)
+        return set_error(FFTSEG_E_INVALID, "plan_create_frames: bad norm %d", norm);
+    if (out_kind != FFTSEG_OUT_COMPLEX && out_kind != FFTSEG_OUT_POWER)
+        return set_error(FFTSEG_E_INVALID, "plan_create_frames: bad out_kind %d", out_kind);
+    if (flags & FFTSEG_FLAG_REAL)
+        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create_frames: frames of a real signal are not built");
+    if (batch > (int64_t(1) << 40) / n || hop > (int64_t(1) << 40) / batch)
+        return set_error(FFTSEG_E_INVALID, "plan_create_frames: batch*n or batch*hop too large");
+    return create_frames(out, n, hop, window, batch, norm, out_kind, flags);
+}
+
 int fftseg_plan_destroy(fftseg_plan p)
 {
     if (!p) return set_error(FFTSEG_E_INVALID, "plan_destroy: NULL plan");
@@ -694,8 +792,8 @@ int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, ff
         return set_error(FFTSEG_E_INVALID, "exec: buffers must be 16-byte aligned");
     if (d_in == d_out && p->out_kind == FFTSEG_OUT_POWER)
         return set_error(FFTSEG_E_INVALID, "exec: the power output cannot be written in place");
-    if (d_in == d_out && p->path == PATH_REAL)
-        return set_error(FFTSEG_E_INVALID, "exec: real-signal plans work out of place only");
+    if (d_in == d_out && (p->path == PATH_REAL || p->path == PATH_FRAMES))
+        return set_error(FFTSEG_E_INVALID, "exec: real-signal and frame plans work out of place only");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -716,11 +814,13 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
     if (!p || !info) return set_error(FFTSEG_E_INVALID, "plan_info: NULL argument");
     info[0] = p->path;
     info[1] = int64_t(1) << p->log_n1;
-    info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL) ? 1 : int64_t(1) << p->log_n2;
-    info[3] = p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
+    info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL || p->path == PATH_FRAMES) ? 1
+                                                                                         : int64_t(1) << p->log_n2;
+    info[3] = p->path == PATH_FRAMES ? p->rchunk * p->n * 8
+              : p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
                                     : p->work ? p->work_segs * p->n * 8
                                               : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
-    info[4] = p->path == PATH_REAL ? p->rchunk : p->work ? p->work_segs : p->ring_cs;
+    info[4] = (p->path == PATH_REAL || p->path == PATH_FRAMES) ? p->rchunk : p->work ? p->work_segs : p->ring_cs;
     info[5] = launches_per_exec(p, p->batch);
     return FFTSEG_OK;
 }

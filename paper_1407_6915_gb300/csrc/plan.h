@@ -12,7 +12,7 @@
 
 namespace fftseg {
 
-enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4, PATH_REAL = 5 };
+enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4, PATH_REAL = 5, PATH_FRAMES = 6 };
 
 }  // namespace fftseg
 
@@ -49,7 +49,11 @@ struct fftseg_plan_s {
     fftseg_plan_s *inner = nullptr;
     float2 *rtw = nullptr;    // w_n^k, k = 0 .. n/4
     float2 *rwork = nullptr;  // [rchunk][n/2] complex intermediate
-    int64_t rchunk = 0;
+    int64_t rchunk = 0;  // segments (real plans) or frames (frame plans) per chunk
+    // overlapping-segment plans (fftseg_plan_create_frames): rwork holds a chunk of frames
+    int64_t hop = 0;
+    int window = 0;
+    float *fwin = nullptr;  // the window, n values (null: rectangular)
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
     // fftseg_exec_host device staging (owned; released with the plan)

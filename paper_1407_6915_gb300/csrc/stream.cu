@@ -96,7 +96,8 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
 {
     if (committed_offset) *committed_offset = start_offset;
     if (!p || !rd || !wr) return set_error(FFTSEG_E_INVALID, "stream: NULL plan or callback");
-    if (p->path == PATH_REAL) return set_error(FFTSEG_E_UNSUPPORTED, "stream: real-signal plans are not streamed");
+    if (p->path == PATH_REAL || p->path == PATH_FRAMES)
+        return set_error(FFTSEG_E_UNSUPPORTED, "stream: real-signal and frame plans are not streamed");
     const int64_t seg_in = p->n * 8;
     const int64_t seg_out = p->n * (p->out_kind == FFTSEG_OUT_POWER ? 4 : 8);
     if (total_bytes < 0 || start_offset < 0 || start_offset > total_bytes || start_offset % seg_in)

@@ -278,3 +278,41 @@ def test_irfft_inverts_rfft(n):
     x = np.random.default_rng(n).standard_normal((4, n))
     assert rel_l2(oracle.irfft(oracle.rfft(x), n, BACK), x) < 1e-12
     assert rel_l2(oracle.irfft(oracle.rfft(x, ORTHO), n, ORTHO), x) < 1e-12
+
+
+# ---- overlapping segments (frames_fft): pinned by reduction to the pinned
+# segment DFT, closed forms of the Hann window, and brute force
+
+def test_frames_with_hop_n_and_no_window_are_segments():
+    n, F = 64, 5
+    x = rand_c128(np.random.default_rng(3), F * n)
+    got = oracle.frames_fft(x, n, n, F, oracle.WINDOW_RECT)
+    assert rel_l2(got, oracle.fft(x.reshape(F, n))) < 1e-14
+
+
+@pytest.mark.parametrize("n,hop", [(16, 8), (64, 17), (256, 64)])
+def test_hann_frames_of_an_on_bin_tone(n, hop):
+    # x[t] = exp(2 pi i m t / n): frame f is the tone times the window, with
+    # phase exp(2 pi i m f hop / n); the periodic Hann window's DFT is
+    # n/2 at 0 and -n/4 at +-1, so X_f = phase * (n/2, -n/4, -n/4 at m, m+-1)
+    m, F = 5, 4
+    t = np.arange((F - 1) * hop + n)
+    x = np.exp(2j * np.pi * ((m * t) % n) / n)
+    got = oracle.frames_fft(x, n, hop, F, oracle.WINDOW_HANN)
+    want = np.zeros((F, n), dtype=np.complex128)
+    for f in range(F):
+        ph = np.exp(2j * np.pi * ((m * f * hop) % n) / n)
+        want[f, m] = ph * n / 2
+        want[f, (m + 1) % n] = -ph * n / 4
+        want[f, (m - 1) % n] = -ph * n / 4
+    assert np.max(np.abs(got - want)) < 1e-9 * n
+
+
+@pytest.mark.parametrize("n,hop,kind", [(8, 3, 0), (16, 5, 1), (32, 32, 1), (16, 20, 0)])
+def test_frames_brute_force(n, hop, kind):
+    F = 4
+    x = rand_c128(np.random.default_rng(n + hop), (F - 1) * hop + n)
+    w = np.ones(n) if kind == 0 else np.array([0.5 - 0.5 * np.cos(2 * np.pi * j / n) for j in range(n)])
+    want = np.stack([brute_dft(x[f * hop: f * hop + n] * w, -1, 1.0) for f in range(F)])
+    assert rel_l2(oracle.frames_fft(x, n, hop, F, kind), want) < 1e-12
+    assert rel_l2(oracle.frames_fft(x, n, hop, F, kind, ORTHO), want / np.sqrt(n)) < 1e-12
