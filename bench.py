@@ -422,6 +422,63 @@ def frames_bench(peak):
             "sizes": rows}
 
 
+def file_bench():
+    """File-backed streaming (fftseg_stream_file): a tones + noise signal file
+    (seed 8; up to 2 GiB, a quarter of the free space at most) in the temporary
+    directory, 2^20-point segments to |X|^2, O_DIRECT where the file system
+    allows it.  The phase split is the analog of the paper's I/O versus FFT
+    breakdown (Sec. IV, Figs. 4-5)."""
+    import shutil
+    import tempfile
+    import torch
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    tmp = tempfile.gettempdir()
+    n = 1 << 20
+    seg = n * 8
+    segs = int(min(2 << 30, shutil.disk_usage(tmp).free // 4) // seg)
+    if segs < 8:
+        return {"unavailable": "less than 8 segments of free space in %s" % tmp}
+    fstype = "unknown"
+    try:
+        best = ""
+        with open("/proc/mounts") as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) > 2 and tmp.startswith(parts[1]) and len(parts[1]) > len(best):
+                    best, fstype = parts[1], parts[2]
+    except OSError:
+        pass
+    src = os.path.join(tmp, "fftseg_bench_signal.c64")
+    dst = os.path.join(tmp, "fftseg_bench_power.f32")
+    try:
+        h = torch.empty(segs * n, dtype=torch.complex64, pin_memory=True)
+        siggen.fill_pointer(siggen.KIND_TONES, 8, 0, segs * n, h.data_ptr())
+        h.numpy().tofile(src)
+        del h
+        plan = fs.Plan(n, 64, fs.FORWARD, out_kind=fs.OUT_POWER)
+        t0 = time.perf_counter()
+        rc, committed = plan.stream_file(src, dst, chunk_segments=64, direct=True)
+        wall = time.perf_counter() - t0
+        ph = plan.stream_phases()
+        io = ph["read_ms"] + ph["write_ms"]
+        return {"file_bytes": segs * seg, "segments": segs, "n": n, "out": "float32 |X|^2", "status": rc,
+                "file_system": fstype, "dir": tmp, "s": round(wall, 3),
+                "in_gbs": round(segs * seg / wall / 1e9, 2),
+                "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+                "share_of_wall": {"file_read": round(ph["read_ms"] / ph["wall_ms"], 3),
+                                  "file_write": round(ph["write_ms"] / ph["wall_ms"], 3),
+                                  "fft": round(ph["fft_ms"] / ph["wall_ms"], 3),
+                                  "h2d_d2h": round((ph["h2d_ms"] + ph["d2h_ms"]) / ph["wall_ms"], 3)},
+                "io_share": round(io / (io + ph["fft_ms"]), 3)}
+    finally:
+        for f in (src, dst):
+            try:
+                os.remove(f)
+            except OSError:
+                pass
+
+
 def tune_table():
     """The autotuner's choice per length (FP32, complex output, a 256 MiB batch)
     beside the library's default schedule."""
@@ -706,6 +763,7 @@ def run_ours(args):
             line["tc_split"] = tc_split(peak)
             line["real"] = real_bench(peak)
             line["frames"] = frames_bench(peak)
+            line["file"] = file_bench()
             line["autotune"] = tune_table()
             line["serve"] = serve_bench(peak)
     if world > 1:

@@ -169,6 +169,26 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
                   int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
                   int64_t *committed_offset);
 
+/*
+ * File-backed streaming: the paper's pipeline end to end on one GPU (Sec. III,
+ * a signal file cut into segments, each transformed, the results written in
+ * positional order).  fftseg_stream with a reader and a writer over files:
+ *   in_path     the complex64 signal; its size is the signal length
+ *   out_path    receives the results at output offset s*n*8 (complex) or
+ *               s*n*4 (power); created, or truncated when start_offset is 0
+ *               (a resumed run keeps what lies before its start)
+ *   start_offset, chunk_segments, committed_offset  as for fftseg_stream
+ *   direct      non-zero: O_DIRECT reads and writes (the page cache bypassed)
+ *               where segment sizes are multiples of 4096 bytes and the file
+ *               system allows it; buffered I/O otherwise
+ * Synchronous.  FFTSEG_E_IO if a file cannot be opened, read or written; the
+ * other results as for fftseg_stream.  The phase split of the run (file reads
+ * and writes against transfers and transforms, the analog of the paper's I/O
+ * versus FFT breakdown, Sec. IV) is in fftseg_stream_phases.
+ */
+int fftseg_stream_file(fftseg_plan p, const char *in_path, const char *out_path, int64_t start_offset,
+                       int64_t chunk_segments, int direct, int64_t *committed_offset);
+
 /* Phase split of the last fftseg_stream call on this plan, in milliseconds
  * (the analog of the paper's I/O versus FFT breakdown, Sec. IV Figs. 4-5):
  * out[0] read callback, out[1] H2D, out[2] transform, out[3] D2H,

@@ -76,6 +76,8 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
+    "fftseg_stream_file": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_autotune": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_double)]),
     "fftseg_exec_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
@@ -243,6 +245,17 @@ class Plan:
                                  ctypes.byref(committed))
         if rc not in (OK, E_IO, E_PARTIAL):
             check(rc, "fftseg_stream")
+        return rc, committed.value
+
+    def stream_file(self, in_path, out_path, start_offset=0, chunk_segments=0, direct=True):
+        """fftseg_stream_file: the signal file through the plan into out_path in
+        positional order.  Returns (status, committed_offset) and does not raise
+        on E_IO/E_PARTIAL."""
+        committed = ctypes.c_int64(0)
+        rc = lib().fftseg_stream_file(self._h, os.fsencode(in_path), os.fsencode(out_path), int(start_offset),
+                                      int(chunk_segments), 1 if direct else 0, ctypes.byref(committed))
+        if rc not in (OK, E_IO, E_PARTIAL):
+            check(rc, "fftseg_stream_file")
         return rc, committed.value
 
     def check(self) -> None:

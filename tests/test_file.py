@@ -1,0 +1,84 @@
+"""File-backed streaming (fftseg_stream_file): the paper's pipeline end to end
+(Sec. III) -- a signal file cut into segments, each transformed, the results
+written to a file in positional order.  The file's results equal, bit for bit,
+the same plan run on the resident signal, and match the FP64 oracle; a resumed
+run completes the output; I/O failures and a partial tail are reported.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import siggen
+from tests._util import rel_l2, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_1407_6915_gb300 as fs  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1407_6915_gb300 import build
+    build.build()
+    assert torch.cuda.is_available()
+
+
+def resident(x, n, out_kind):
+    plan = fs.Plan(n, x.size // n, fs.FORWARD, out_kind=out_kind)
+    y = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    return y.cpu().numpy().ravel()
+
+
+@pytest.mark.parametrize("direct", [True, False])
+@pytest.mark.parametrize("n,B,chunk,out_kind", [(256, 300, 64, fs.OUT_COMPLEX), (4096, 70, 16, fs.OUT_COMPLEX),
+                                                (1 << 16, 11, 4, fs.OUT_POWER)])
+def test_file_stream_equals_resident_and_oracle(tmp_path, n, B, chunk, out_kind, direct):
+    x = siggen.tones(950 + n, B * n)
+    src, dst = tmp_path / "signal.c64", tmp_path / "spectra.out"
+    x.tofile(src)
+    plan = fs.Plan(n, chunk, fs.FORWARD, out_kind=out_kind)
+    rc, committed = plan.stream_file(src, dst, chunk_segments=chunk, direct=direct)
+    assert rc == fs.OK and committed == B * n * 8
+    got = np.fromfile(dst, dtype=np.float32 if out_kind == fs.OUT_POWER else np.complex64)
+    np.testing.assert_array_equal(got, resident(x, n, out_kind))
+    k = np.r_[0, B - 1]
+    ref = oracle.fft(x.reshape(B, n)[k])
+    if out_kind == fs.OUT_POWER:
+        assert rel_l2(got.reshape(B, n)[k], ref.real ** 2 + ref.imag ** 2) <= 2 * tol_fp32(n)
+    else:
+        assert rel_l2(got.reshape(B, n)[k], ref) <= tol_fp32(n)
+    ph = plan.stream_phases()
+    assert ph["read_ms"] > 0 and ph["write_ms"] > 0 and ph["wall_ms"] > 0
+
+
+def test_file_stream_resumes(tmp_path):
+    n, B, chunk = 4096, 40, 8
+    x = siggen.tones(977, B * n)
+    src, dst = tmp_path / "signal.c64", tmp_path / "spectra.out"
+    x.tofile(src)
+    plan = fs.Plan(n, chunk, fs.FORWARD)
+    assert plan.stream_file(src, dst, chunk_segments=chunk)[0] == fs.OK
+    full = np.fromfile(dst, dtype=np.complex64)
+    # lose the second half of the output, then resume from segment 24
+    part = full.copy()
+    part[24 * n:] = 0
+    part.tofile(dst)
+    rc, committed = plan.stream_file(src, dst, start_offset=24 * n * 8, chunk_segments=chunk)
+    assert rc == fs.OK and committed == B * n * 8
+    np.testing.assert_array_equal(np.fromfile(dst, dtype=np.complex64), full)
+
+
+def test_file_stream_errors(tmp_path):
+    n = 1024
+    plan = fs.Plan(n, 4, fs.FORWARD)
+    rc, committed = plan.stream_file(tmp_path / "missing.c64", tmp_path / "o.out")
+    assert rc == fs.E_IO and committed == 0
+    x = siggen.uniform(3, 5 * n + 100)  # five segments and a partial one
+    x.tofile(tmp_path / "tail.c64")
+    rc, committed = plan.stream_file(tmp_path / "tail.c64", tmp_path / "t.out", chunk_segments=4)
+    assert rc == fs.E_PARTIAL and committed == 5 * n * 8
+    got = np.fromfile(tmp_path / "t.out", dtype=np.complex64)
+    assert got.size == 5 * n
+    np.testing.assert_array_equal(got, resident(x[: 5 * n], n, fs.OUT_COMPLEX))
