@@ -91,7 +91,124 @@ __global__ void __launch_bounds__(kRealThreads) k_real_pre(const RealArgs a)
     }
 }
 
+// Forward real segments of n = 2L <= 8192 points in one pass: the block
+// kernel's persistent CTAs and bulk-copied tiles of whole segments (the L
+// complex values of each), the L-point Stockham FFT, then the split above
+// inside the tile: Z goes to the tile buffer in natural order and every
+// thread forms bin pairs (k, L - k) of one segment, written as n/2 + 1 bins.
+template <int LOG_L>
+__global__ void __launch_bounds__(256, 2) k_block_r2c(const RealBlockArgs a)
+{
+    using Sh = BlockShape<LOG_L>;
+    constexpr int L = 1 << LOG_L, W = 1 << Sh::LOG_W, E = Sh::E, T = Sh::T, V = E / T;
+    constexpr int PAIRS = L / 2 + 1;
+    extern __shared__ __align__(1024) float2 sm[];
+    float2 *P = sm;
+    float2 *X = sm + 2 * E;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(X + Sh::SLOTS);
+    const int tid = threadIdx.x;
+    if (smem_u32(P) & 127) {
+        if (tid == 0) atomicOr(a.err, 2);
+        return;
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int64_t u, int b) {
+        if (tid == 0) {
+            int64_t segs = a.nseg - u * W;
+            if (segs > W) segs = W;
+            const uint32_t bytes = (uint32_t)(segs * L * (int64_t)sizeof(float2));
+            fence_proxy_async();
+            mbar_expect_tx(&bar[b], bytes);
+            tma_load_1d(P + b * E, a.in + u * E, bytes, &bar[b]);
+        }
+    };
+    int64_t u = blockIdx.x;
+    if (u < a.ntiles) issue(u, 0);
+    for (int k = 0; u < a.ntiles; u += gridDim.x, ++k) {
+        const int b = k & 1;
+        if (u + gridDim.x < a.ntiles) issue(u + gridDim.x, b ^ 1);
+        mbar_wait(&bar[b], (k >> 1) & 1, a.err);
+        float2 *Pb = P + b * E;
+        float2 v[V];
+        gather<LOG_L, Sh::LOG_W, false, T, 0>(v, [&](int c, int i) { return Pb[(c << LOG_L) + i]; });
+        run_stages<LOG_L, Sh::LOG_W, false, -1, T, Sh::PS, 0, false>(v, X, a.twL);
+        // Z of every segment of the tile, natural order, into the tile buffer
+        // (its last reads were the gather, ordered by the stages' barriers)
+        scatter_last<LOG_L, Sh::LOG_W, false, T>(v, [&](int c, int i, float2 x) { Pb[(c << LOG_L) + i] = x; });
+        __syncthreads();
+        const int64_t line0 = u * W;
+        for (int p = tid; p < W * PAIRS; p += T) {
+            const int c = p / PAIRS, kk = p - c * PAIRS;
+            const int64_t seg = line0 + c;
+            if (seg >= a.nseg) continue;
+            const float2 A = Pb[(c << LOG_L) + kk];
+            const float2 B = conjf2(Pb[(c << LOG_L) + ((L - kk) & (L - 1))]);
+            const float2 fe = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y + B.y));
+            const float2 fo = make_float2(0.5f * (A.y - B.y), -0.5f * (A.x - B.x));
+            const float2 wfo = cmul(__ldg(a.tw + kk), fo);
+            const float2 xk = scalef2(make_float2(fe.x + wfo.x, fe.y + wfo.y), a.scale);
+            const float2 xm = scalef2(make_float2(fe.x - wfo.x, -(fe.y - wfo.y)), a.scale);
+            const int64_t o = seg * (L + 1);
+            if (a.out_power) {
+                float *Q = static_cast<float *>(a.out) + o;
+                Q[kk] = xk.x * xk.x + xk.y * xk.y;
+                if (2 * kk != L) Q[L - kk] = xm.x * xm.x + xm.y * xm.y;
+            } else {
+                float2 *Q = static_cast<float2 *>(a.out) + o;
+                Q[kk] = xk;
+                if (2 * kk != L) Q[L - kk] = xm;
+            }
+        }
+        __syncthreads();  // P[b] and X read in full before they are reused
+    }
+}
+
+template <int LOG_L>
+cudaError_t block_r2c_t(const RealBlockArgs &a, cudaStream_t st)
+{
+    using B = BlockShape<LOG_L>;
+    auto k = k_block_r2c<LOG_L>;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
+        if (e != cudaSuccess) return e;
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B::T, B::SMEM);
+        if (e != cudaSuccess) return e;
+        per_sm = occ > 0 ? occ : 1;
+    }
+    if (a.ntiles == 0) return cudaSuccess;
+    int64_t grid = (int64_t)per_sm * device_sm_count();
+    if (grid > a.ntiles) grid = a.ntiles;
+    k<<<(unsigned)grid, B::T, B::SMEM, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_block_r2c(int log_l, const RealBlockArgs &a, cudaStream_t st)
+{
+    switch (log_l) {
+        case 1: return block_r2c_t<1>(a, st);
+        case 2: return block_r2c_t<2>(a, st);
+        case 3: return block_r2c_t<3>(a, st);
+        case 4: return block_r2c_t<4>(a, st);
+        case 5: return block_r2c_t<5>(a, st);
+        case 6: return block_r2c_t<6>(a, st);
+        case 7: return block_r2c_t<7>(a, st);
+        case 8: return block_r2c_t<8>(a, st);
+        case 9: return block_r2c_t<9>(a, st);
+        case 10: return block_r2c_t<10>(a, st);
+        case 11: return block_r2c_t<11>(a, st);
+        case 12: return block_r2c_t<12>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 cudaError_t launch_real(bool post, bool power, RealArgs a, int64_t nseg, cudaStream_t st)
 {

@@ -52,6 +52,20 @@ struct RealArgs {
     float scale;
 };
 cudaError_t launch_real(bool post, bool power, RealArgs a, int64_t nseg, cudaStream_t st);
+// Forward real segments of n = 2^(log_l + 1) <= 8192 points in one pass (the
+// block kernel's tiles with the split fused): in [nseg][2^log_l] complex64 view
+// of the samples -> out [nseg][2^log_l + 1] bins (or float32 |X|^2).
+struct RealBlockArgs {
+    const float2 *in;
+    void *out;
+    const float2 *twL;  // stage tables of the 2^log_l-point line
+    const float2 *tw;   // w_n^k, k <= 2^(log_l - 1)
+    int *err;
+    int64_t nseg, ntiles;
+    int out_power;
+    float scale;
+};
+cudaError_t launch_block_r2c(int log_l, const RealBlockArgs &a, cudaStream_t st);
 // Overlapping segments (frames.cu): windowed frames f = samples
 // [f*hop, f*hop + n) of the signal into [nframes][n] complex64.
 struct FramesArgs {

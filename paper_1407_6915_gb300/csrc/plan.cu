@@ -292,6 +292,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_FOURSTEP: return 1;
         case PATH_REAL:
         case PATH_FRAMES: {
+            if (p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) return 1;
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
                 k += 1 + launches_per_exec(p->inner, nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk);
@@ -355,10 +356,28 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
         return FFTSEG_OK;
     }
     if (p->path == PATH_REAL) {
-        // chunks of rchunk segments: the complex FFT of n/2 points and the
-        // split (forward) or join (inverse) pass, through an L2-sized intermediate
         const int64_t M = p->n / 2;
         const bool power = p->out_kind == FFTSEG_OUT_POWER;
+        if (p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) {
+            // n/2 <= 4096: one pass, the split fused into the block kernel's tiles
+            RealBlockArgs a{};
+            const int64_t W = block_segments_per_cta(p->inner->log_n);
+            a.in = static_cast<const float2 *>(d_in);
+            a.out = d_out;
+            a.twL = p->inner->twA;
+            a.tw = p->rtw;
+            a.err = p->d_err;
+            a.nseg = nseg;
+            a.ntiles = (nseg + W - 1) / W;
+            a.out_power = power;
+            a.scale = p->scale;
+            cudaError_t e = launch_block_r2c(p->inner->log_n, a, st);
+            if (e != cudaSuccess) return cuda_error(e, "real-signal block kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
+        // otherwise chunks of rchunk segments: the complex FFT of n/2 points and
+        // the split (forward) or join (inverse) pass, through an L2-sized intermediate
         for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
             const int64_t cnt = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
             RealArgs a{};
