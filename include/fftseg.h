@@ -53,7 +53,7 @@ typedef enum {
     FFTSEG_E_IO = -4,          /* a reader or writer callback failed */
     FFTSEG_E_PARTIAL = -5,     /* the signal ends inside a segment and zero padding is off */
     FFTSEG_E_TIMEOUT = -6,     /* a bounded wait ran out (server poll, device wait) */
-    FFTSEG_E_UNSUPPORTED = -7  /* n not a power of two in [2, 2^24], or a precision/size mix not built */
+    FFTSEG_E_UNSUPPORTED = -7  /* n outside the built lengths, or a precision/size mix not built */
 } fftseg_status;
 
 enum { FFTSEG_FORWARD = -1, FFTSEG_INVERSE = +1 };
@@ -96,7 +96,12 @@ typedef struct fftseg_plan_s *fftseg_plan;
  * over a block of segments).  Twiddle tables are evaluated in double
  * precision on the host and rounded once to float32 (split into hi+lo halves
  * for the tensor-core precisions); they stay resident on the current device.
- *   n          power of two, 2 <= n <= 2^24, else FFTSEG_E_UNSUPPORTED
+ *   n          a power of two, 2 <= n <= 2^24; or any other length 3 <= n <= 2^23
+ *              (FP32 only), run by Bluestein's chirp-z identity as a cyclic
+ *              convolution over M = 2^ceil(log2(2n - 1)) points: chirp in, M-point
+ *              FFT, product with the plan's chirp spectrum, M-point inverse FFT,
+ *              chirp out (five launches per chunk of at most 32 MiB of M-point
+ *              rows; out of place only); else FFTSEG_E_UNSUPPORTED
  *   batch      >= 1: the most segments one fftseg_exec call processes
  *   direction  FFTSEG_FORWARD or FFTSEG_INVERSE
  *   norm       FFTSEG_NORM_*
@@ -239,7 +244,8 @@ int fftseg_plan_destroy(fftseg_plan p);
 
 /* Plan facts: info[0] path (0 block, 1 cluster, 2 two-pass, 3 tensor core,
  * 4 persistent four-step, 5 real signal over an inner complex plan,
- * 6 overlapping frames over an inner complex plan),
+ * 6 overlapping frames over an inner complex plan, 7 a length that is not a
+ * power of two, over two inner plans of M points; info[1] is then M),
  * info[1] n1, info[2] n2, info[3] workspace bytes, info[4] segments per
  * workspace chunk, info[5] kernel launches per fftseg_exec of a full batch. */
 int fftseg_plan_info(fftseg_plan p, int64_t info[6]);

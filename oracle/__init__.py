@@ -39,6 +39,10 @@ def _load():
             fn.restype = ctypes.c_int
             fn.argtypes = [ptr_t, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                            ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        fn = lib.oracle_dft_c64
+        fn.restype = ctypes.c_int
+        fn.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                       ctypes.c_void_p, ctypes.c_int64, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -136,3 +140,24 @@ def frames_fft(x, n: int, hop: int, nframes: int, kind: int = WINDOW_HANN, norm:
     idx = np.arange(nframes)[:, None] * hop + np.arange(n)[None, :]
     fr = x.astype(np.complex128)[idx] * window(n, kind)[None, :]
     return fft(fr, FORWARD, norm, nthreads)
+
+
+def dft(x, direction: int = FORWARD, norm: int = NORM_NONE, bins=None, nthreads: int = None) -> np.ndarray:
+    """Direct DFT of complex64 segments of any length n (last axis), the
+    definition written out with the exponent index (j*k mod n) reduced exactly:
+    X[k] = scale * sum_j x[j] exp(sigma 2 pi i j k / n).  `bins`: compute only
+    these k (all n when None).  Returns complex128 [.., nbins]."""
+    lib = _load()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.complex64))
+    n = x.shape[-1]
+    nseg = int(np.prod(x.shape[:-1], dtype=np.int64)) if x.ndim > 1 else 1
+    b = None if bins is None else np.ascontiguousarray(np.asarray(bins, dtype=np.int64))
+    nb = n if b is None else b.size
+    out = np.empty(x.shape[:-1] + (nb,), dtype=np.complex128)
+    if nseg == 0 or n == 0 or nb == 0:
+        return out
+    rc = lib.oracle_dft_c64(x.ctypes.data, out.ctypes.data, n, nseg, int(direction), int(norm),
+                            None if b is None else b.ctypes.data, int(nb), int(nthreads or default_threads()))
+    if rc != 0:
+        raise ValueError("oracle rejected the arguments (status %d)" % rc)
+    return out

@@ -26,6 +26,9 @@
  *   5. scale.
  * Segments are independent; they are spread over POSIX threads.
  *
+ * Lengths that are not powers of two: oracle_dft_c64 (end of file) is the
+ * definition itself, a direct sum over a table of the n roots of unity.
+ *
  * Parity: pinned by the tests against a brute-force O(n^2) DFT, the impulse
  * and pure-tone closed forms, Parseval, linearity, the shift theorem,
  * conjugate symmetry and the inverse round trip (tests/test_oracle.py).
@@ -185,4 +188,102 @@ int oracle_fft_c128(const double *in, double *out, int64_t n, int64_t nseg, int 
                     int nthreads)
 {
     return run(NULL, in, out, n, nseg, sigma, norm, nthreads);
+}
+
+/*
+ * Direct DFT of any length n >= 1, the definition written out:
+ *   X_s[k] = scale * sum_j x_s[j] * r[(j*k) mod n],  r[m] = exp(sigma*2*pi*i*m/n),
+ * the exponent index reduced exactly in integers, the n roots r[m] evaluated
+ * by libm once per call.  Only the bins listed in `bins` (nbins of them, each
+ * in [0, n)) are computed, or all n when bins is NULL.  Complex64 input,
+ * complex128 output [nseg][nbins].  It serves lengths that are not powers of
+ * two, where the radix-2 recursion above does not apply, and spot checks of
+ * single bins at large n.
+ */
+typedef struct {
+    const float *in;
+    double *out;
+    const double *roots; /* [n][2] */
+    const int64_t *bins; /* NULL: every bin */
+    int64_t n, nb;
+    int64_t seg_begin, seg_end;
+    double scale;
+} djob_t;
+
+static void *run_djob(void *arg)
+{
+    djob_t *jb = (djob_t *)arg;
+    const int64_t n = jb->n;
+    for (int64_t s = jb->seg_begin; s < jb->seg_end; ++s) {
+        const float *x = jb->in + 2 * s * n;
+        double *X = jb->out + 2 * s * jb->nb;
+        for (int64_t b = 0; b < jb->nb; ++b) {
+            const int64_t k = jb->bins ? jb->bins[b] : b;
+            double re = 0.0, im = 0.0;
+            int64_t m = 0; /* (j*k) mod n, advanced by k each step */
+            for (int64_t j = 0; j < n; ++j) {
+                const double xr = (double)x[2 * j], xi = (double)x[2 * j + 1];
+                const double wr = jb->roots[2 * m], wi = jb->roots[2 * m + 1];
+                re += xr * wr - xi * wi;
+                im += xr * wi + xi * wr;
+                m += k;
+                if (m >= n) m -= n;
+            }
+            X[2 * b] = re * jb->scale;
+            X[2 * b + 1] = im * jb->scale;
+        }
+    }
+    return NULL;
+}
+
+int oracle_dft_c64(const float *in, double *out, int64_t n, int64_t nseg, int sigma, int norm,
+                   const int64_t *bins, int64_t nbins, int nthreads)
+{
+    if (!in || !out || n < 1 || nseg < 0 || (sigma != -1 && sigma != 1) || norm < 0 || norm > 2)
+        return ORACLE_E_INVALID;
+    if (bins)
+        for (int64_t b = 0; b < nbins; ++b)
+            if (bins[b] < 0 || bins[b] >= n) return ORACLE_E_INVALID;
+    if (nseg == 0) return ORACLE_OK;
+    double *roots = (double *)malloc(sizeof(double) * 2 * (size_t)n);
+    if (!roots) return ORACLE_E_NOMEM;
+    for (int64_t m = 0; m < n; ++m) {
+        const double a = kTwoPi * ((double)m / (double)n);
+        roots[2 * m] = cos(a);
+        roots[2 * m + 1] = (double)sigma * sin(a);
+    }
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > nseg) nthreads = (int)nseg;
+    djob_t *jobs = (djob_t *)calloc((size_t)nthreads, sizeof(djob_t));
+    pthread_t *tid = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !tid) {
+        free(jobs);
+        free(tid);
+        free(roots);
+        return ORACLE_E_NOMEM;
+    }
+    const double scale = norm_scale(n, sigma, norm);
+    for (int t = 0; t < nthreads; ++t) {
+        jobs[t].in = in;
+        jobs[t].out = out;
+        jobs[t].roots = roots;
+        jobs[t].bins = bins;
+        jobs[t].n = n;
+        jobs[t].nb = bins ? nbins : n;
+        jobs[t].seg_begin = nseg * t / nthreads;
+        jobs[t].seg_end = nseg * (t + 1) / nthreads;
+        jobs[t].scale = scale;
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&tid[t], NULL, run_djob, &jobs[t]) != 0) break;
+        started = t;
+    }
+    run_djob(&jobs[0]);
+    for (int t = started + 1; t < nthreads; ++t) run_djob(&jobs[t]);
+    for (int t = 1; t <= started; ++t) pthread_join(tid[t], NULL);
+    free(jobs);
+    free(tid);
+    free(roots);
+    return ORACLE_OK;
 }

@@ -28,7 +28,7 @@ FLAG_REAL = 0x20
 
 WINDOW_RECT, WINDOW_HANN = 0, 1
 PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step", 5: "real",
-              6: "frames"}
+              6: "frames", 7: "bluestein"}
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_IO, E_PARTIAL, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 

@@ -77,6 +77,20 @@ struct FramesArgs {
     int n;
 };
 cudaError_t launch_frames(FramesArgs a, int64_t nframes, cudaStream_t st);
+// Lengths that are not powers of two (bluestein.cu): step 0 chirps x into the
+// M-point work rows (zero-padded), step 1 multiplies them by B, step 2 chirps
+// the first n points out into d_out ([nseg][n], complex64 or float32 |X|^2,
+// times scale).  nseg <= 65535 per launch.
+struct BlueArgs {
+    const float2 *x;     // step 0: [nseg][n]
+    float2 *work;        // [nseg][m]
+    void *out;           // step 2
+    const float2 *w;     // chirp, n values
+    const float2 *bhat;  // FFT_M of the conjugate chirp, divided by M
+    int64_t n, m;
+    float scale;
+};
+cudaError_t launch_blue(int step, bool power, const BlueArgs &a, int64_t nseg, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

@@ -128,6 +128,9 @@ void free_plan(fftseg_plan p)
 {
     if (!p) return;
     free_plan(p->inner);
+    free_plan(p->inner2);
+    cudaFree(p->bw);
+    cudaFree(p->bhat);
     cudaFree(p->rtw);
     cudaFree(p->rwork);
     cudaFree(p->fwin);
@@ -290,6 +293,14 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
+        case PATH_BLUESTEIN: {
+            int64_t k = 0;
+            for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
+                const int64_t c = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
+                k += 3 + launches_per_exec(p->inner, c) + launches_per_exec(p->inner2, c);
+            }
+            return k;
+        }
         case PATH_REAL:
         case PATH_FRAMES: {
             if (p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) return 1;
@@ -334,6 +345,35 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
+    if (p->path == PATH_BLUESTEIN) {
+        // chunks of rchunk segments: chirp in, M-point forward transform,
+        // product with B, M-point inverse transform, chirp out
+        const bool power = p->out_kind == FFTSEG_OUT_POWER;
+        for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
+            const int64_t cnt = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
+            BlueArgs a{};
+            a.x = static_cast<const float2 *>(d_in) + s0 * p->n;
+            a.work = p->rwork;
+            a.out = static_cast<char *>(d_out) + s0 * p->n * (power ? 4 : 8);
+            a.w = p->bw;
+            a.bhat = p->bhat;
+            a.n = p->n;
+            a.m = p->bm;
+            a.scale = p->scale;
+            cudaError_t e = launch_blue(0, power, a, cnt, st);
+            if (e != cudaSuccess) return cuda_error(e, "chirp-in launch");
+            int rc = exec_plan(p->inner, p->rwork, p->rwork, cnt, st);
+            if (rc != FFTSEG_OK) return rc;
+            e = launch_blue(1, power, a, cnt, st);
+            if (e != cudaSuccess) return cuda_error(e, "chirp product launch");
+            rc = exec_plan(p->inner2, p->rwork, p->rwork, cnt, st);
+            if (rc != FFTSEG_OK) return rc;
+            e = launch_blue(2, power, a, cnt, st);
+            if (e != cudaSuccess) return cuda_error(e, "chirp-out launch");
+            count_launches(3);
+        }
+        return FFTSEG_OK;
+    }
     if (p->path == PATH_FRAMES) {
         // chunks of rchunk frames: windowed frames into an L2-sized
         // intermediate, then the batched complex plan of n points
@@ -704,6 +744,84 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
     return FFTSEG_OK;
 }
 
+// Length n that is not a power of two: Bluestein over M = 2^ceil(log2(2n - 1))
+// (see bluestein.cu).  The chirp w[m] = exp(sigma pi i m^2 / n), its phase
+// reduced exactly as (m^2 mod 2n) / n, and b = conj(w) placed cyclically and
+// divided by M (exact) are evaluated in double on the host; B = FFT_M(b) is
+// computed once on the device with the plan's own forward M-point plan.
+int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int out_kind,
+                     unsigned flags)
+{
+    fftseg_plan p = new (std::nothrow) fftseg_plan_s();
+    if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    int64_t M = 2;
+    while (M < 2 * n - 1) M *= 2;
+    p->n = n;
+    p->batch = batch;
+    p->log_n = ilog2(M);
+    p->log_n1 = p->log_n;
+    p->direction = direction;
+    p->norm = norm;
+    p->precision = FFTSEG_PREC_FP32;
+    p->out_kind = out_kind;
+    p->flags = flags;
+    p->path = PATH_BLUESTEIN;
+    p->bm = M;
+    if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
+    else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
+    int64_t cs = kRealChunkBytes / (M * 8);
+    if (cs < 1) cs = 1;
+    if (cs > 65535) cs = 65535;
+    if (cs > batch) cs = batch;
+    p->rchunk = cs;
+    int rc = fftseg_plan_create(&p->inner, M, cs, FFTSEG_FORWARD, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
+                                FFTSEG_OUT_COMPLEX, flags);
+    if (rc == FFTSEG_OK)
+        rc = fftseg_plan_create(&p->inner2, M, cs, FFTSEG_INVERSE, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
+                                FFTSEG_OUT_COMPLEX, flags);
+    if (rc == FFTSEG_OK) {
+        const double pi = 3.141592653589793238462643383279;
+        std::vector<float2> w((size_t)n), b((size_t)M, make_float2(0.f, 0.f));
+        const double inv_m = 1.0 / (double)M;
+        for (int64_t m = 0; m < n; ++m) {
+            const int64_t e2 = (int64_t)(((unsigned __int128)m * (unsigned __int128)m) % (unsigned __int128)(2 * n));
+            const double a = pi * ((double)e2 / (double)n);
+            const double c = cos(a), sn = (double)direction * sin(a);
+            w[(size_t)m] = make_float2((float)c, (float)sn);
+            const float2 cb = make_float2((float)(c * inv_m), (float)(-sn * inv_m));  // conj(w) / M
+            b[(size_t)m] = cb;
+            if (m > 0) b[(size_t)(M - m)] = cb;
+        }
+        rc = upload(&p->bw, w);
+        float2 *bdev = nullptr;
+        if (rc == FFTSEG_OK) rc = upload(&bdev, b);
+        if (rc == FFTSEG_OK) {
+            e = cudaMalloc((void **)&p->bhat, (size_t)M * sizeof(float2));
+            if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(chirp spectrum)");
+        }
+        if (rc == FFTSEG_OK) rc = exec_plan(p->inner, bdev, p->bhat, 1, nullptr);
+        if (rc == FFTSEG_OK) rc = fftseg_plan_check(p->inner);  // synchronises
+        cudaFree(bdev);
+    }
+    if (rc == FFTSEG_OK) {
+        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
+        if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(Bluestein rows)");
+    }
+    if (rc != FFTSEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FFTSEG_OK;
+}
+
 }  // namespace fftseg
 
 using namespace fftseg;
@@ -715,8 +833,10 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
 {
     if (!out) return set_error(FFTSEG_E_INVALID, "plan_create: out is NULL");
     *out = nullptr;
-    if (!is_pow2(n) || n < 2 || n > (int64_t(1) << FFTSEG_MAX_LOG2N))
-        return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: n=%lld is not a power of two in [2, 2^24]",
+    if (n < 2 || n > (int64_t(1) << FFTSEG_MAX_LOG2N) ||
+        (!is_pow2(n) && n > (int64_t(1) << (FFTSEG_MAX_LOG2N - 1))))
+        return set_error(FFTSEG_E_UNSUPPORTED,
+                         "plan_create: n=%lld outside [2, 2^24] (powers of two) or [3, 2^23] (other lengths)",
                          (long long)n);
     if (batch < 1) return set_error(FFTSEG_E_INVALID, "plan_create: batch must be >= 1");
     if (direction != FFTSEG_FORWARD && direction != FFTSEG_INVERSE)
@@ -729,7 +849,15 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
         return set_error(FFTSEG_E_INVALID, "plan_create: bad precision %d", precision);
     if (batch > (int64_t(1) << 40) / n)
         return set_error(FFTSEG_E_INVALID, "plan_create: batch*n too large");
-    if (flags & FFTSEG_FLAG_REAL) return create_real(out, n, batch, direction, norm, precision, out_kind, flags);
+    if (flags & FFTSEG_FLAG_REAL) {
+        if (!is_pow2(n)) return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: real-signal plans need a power of two");
+        return create_real(out, n, batch, direction, norm, precision, out_kind, flags);
+    }
+    if (!is_pow2(n)) {
+        if (precision != FFTSEG_PREC_FP32)
+            return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: lengths that are not powers of two are FP32 only");
+        return create_bluestein(out, n, batch, direction, norm, out_kind, flags);
+    }
     if (flags & FFTSEG_FLAG_AUTOTUNE) {  // replace the schedule flags by the fastest measured schedule
         unsigned chosen = 0;
         const int trc = tune_schedule(n, batch, precision, out_kind, &chosen, nullptr);
@@ -811,7 +939,7 @@ int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, ff
         return set_error(FFTSEG_E_INVALID, "exec: buffers must be 16-byte aligned");
     if (d_in == d_out && p->out_kind == FFTSEG_OUT_POWER)
         return set_error(FFTSEG_E_INVALID, "exec: the power output cannot be written in place");
-    if (d_in == d_out && (p->path == PATH_REAL || p->path == PATH_FRAMES))
+    if (d_in == d_out && (p->path == PATH_REAL || p->path == PATH_FRAMES || p->path == PATH_BLUESTEIN))
         return set_error(FFTSEG_E_INVALID, "exec: real-signal and frame plans work out of place only");
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -833,13 +961,17 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
     if (!p || !info) return set_error(FFTSEG_E_INVALID, "plan_info: NULL argument");
     info[0] = p->path;
     info[1] = int64_t(1) << p->log_n1;
-    info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL || p->path == PATH_FRAMES) ? 1
-                                                                                         : int64_t(1) << p->log_n2;
-    info[3] = p->path == PATH_FRAMES ? p->rchunk * p->n * 8
+    info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL || p->path == PATH_FRAMES ||
+               p->path == PATH_BLUESTEIN)
+                  ? 1
+                  : int64_t(1) << p->log_n2;
+    info[3] = p->path == PATH_BLUESTEIN ? p->rchunk * p->bm * 8
+              : p->path == PATH_FRAMES ? p->rchunk * p->n * 8
               : p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
                                     : p->work ? p->work_segs * p->n * 8
                                               : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
-    info[4] = (p->path == PATH_REAL || p->path == PATH_FRAMES) ? p->rchunk : p->work ? p->work_segs : p->ring_cs;
+    info[4] = (p->path == PATH_REAL || p->path == PATH_FRAMES || p->path == PATH_BLUESTEIN) ? p->rchunk
+              : p->work ? p->work_segs : p->ring_cs;
     info[5] = launches_per_exec(p, p->batch);
     return FFTSEG_OK;
 }

@@ -12,7 +12,15 @@
 
 namespace fftseg {
 
-enum Path { PATH_BLOCK = 0, PATH_CLUSTER = 1, PATH_TWOPASS = 2, PATH_FOURSTEP = 4, PATH_REAL = 5, PATH_FRAMES = 6 };
+enum Path {
+    PATH_BLOCK = 0,
+    PATH_CLUSTER = 1,
+    PATH_TWOPASS = 2,
+    PATH_FOURSTEP = 4,
+    PATH_REAL = 5,
+    PATH_FRAMES = 6,
+    PATH_BLUESTEIN = 7
+};
 
 }  // namespace fftseg
 
@@ -54,6 +62,12 @@ struct fftseg_plan_s {
     int64_t hop = 0;
     int window = 0;
     float *fwin = nullptr;  // the window, n values (null: rectangular)
+    // lengths that are not powers of two: inner (forward) and inner2 (inverse)
+    // M-point plans, the chirp and B = FFT_M(conjugate chirp) / M; rwork holds
+    // a chunk of M-point rows
+    fftseg_plan_s *inner2 = nullptr;
+    float2 *bw = nullptr, *bhat = nullptr;
+    int64_t bm = 0;
     // fftseg_stream phase split of the last call (ms)
     double phases[6] = {0, 0, 0, 0, 0, 0};
     // fftseg_exec_host device staging (owned; released with the plan)

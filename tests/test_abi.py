@@ -42,11 +42,17 @@ def _create(n, batch=1, direction=fs.FORWARD, norm=fs.NORM_NONE, prec=fs.PREC_FP
     return rc, h
 
 
-@pytest.mark.parametrize("n", [0, 1, 3, 12, 1000, (1 << 24) + 1, 1 << 25])
+@pytest.mark.parametrize("n", [0, 1, (1 << 23) + 1, (1 << 24) + 1, 1 << 25])
 def test_plan_rejects_bad_lengths(n):
+    # powers of two up to 2^24, other lengths (Bluestein) up to 2^23
     rc, h = _create(n)
     assert rc == fs.E_UNSUPPORTED and not h.value
-    assert "power of two" in fs.last_error()
+    assert "outside" in fs.last_error()
+
+
+def test_other_lengths_are_fp32_only():
+    rc, h = _create(1000, prec=fs.PREC_TC_FP16)
+    assert rc == fs.E_UNSUPPORTED and not h.value
 
 
 @pytest.mark.parametrize("kw", [dict(batch=0), dict(direction=0), dict(direction=2), dict(norm=7),

@@ -316,3 +316,32 @@ def test_frames_brute_force(n, hop, kind):
     want = np.stack([brute_dft(x[f * hop: f * hop + n] * w, -1, 1.0) for f in range(F)])
     assert rel_l2(oracle.frames_fft(x, n, hop, F, kind), want) < 1e-12
     assert rel_l2(oracle.frames_fft(x, n, hop, F, kind, ORTHO), want / np.sqrt(n)) < 1e-12
+
+
+# ---- the direct DFT (any length): pinned against the radix-2 oracle where
+# both apply, numpy elsewhere, and the impulse closed form
+
+@pytest.mark.parametrize("n", [1, 2, 8, 64, 512])
+def test_direct_dft_equals_radix2_at_powers_of_two(n):
+    x = rand_c128(np.random.default_rng(n), (3, n)).astype(np.complex64)
+    for sigma, norm in ((FWD, NONE), (INV, BACK), (FWD, ORTHO)):
+        assert rel_l2(oracle.dft(x, sigma, norm), oracle.fft(x, sigma, norm)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [3, 5, 6, 7, 12, 100, 1000, 1001, 4093])
+def test_direct_dft_matches_numpy(n):
+    x = rand_c128(np.random.default_rng(n), (2, n)).astype(np.complex64)
+    xc = x.astype(np.complex128)
+    assert rel_l2(oracle.dft(x), np.fft.fft(xc)) < 1e-12
+    assert rel_l2(oracle.dft(x, INV, BACK), np.fft.ifft(xc)) < 1e-12
+
+
+@pytest.mark.parametrize("n,j0", [(12, 5), (1001, 700)])
+def test_direct_dft_impulse_and_bins(n, j0):
+    x = np.zeros(n, dtype=np.complex64)
+    x[j0] = 1
+    k = np.arange(n)
+    want = np.exp(-2j * np.pi * ((j0 * k) % n) / n)
+    assert np.max(np.abs(oracle.dft(x) - want)) < 1e-12
+    sel = np.array([0, n - 1, 7 % n, n // 2])
+    assert np.max(np.abs(oracle.dft(x, bins=sel) - want[sel])) < 1e-12
