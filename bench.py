@@ -154,14 +154,19 @@ def cpu_baseline(seconds_target=12.0):
                       % (seg, reps, dt)}
 
 
-def kernel_rev():
-    """Hash of the kernel sources (device code): a DRAM-traffic figure only applies to
-    the kernels it was taken on."""
+# the translation unit that instantiates each path's kernel
+KERNEL_TU = {"four-step": "k_fourstep.cu", "cluster": "k_cluster.cu", "block": "k_lines.cu"}
+
+
+def kernel_rev(path="four-step"):
+    """Hash of the device code of a path's kernel (every kernel header and the
+    path's translation unit): a DRAM-traffic figure only applies to the kernel
+    sources it was taken on."""
     import hashlib
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1407_6915_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith(".cuh") or (name.startswith("k_") and name.endswith(".cu")):
+        if name.endswith(".cuh") or name == KERNEL_TU.get(path):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:12]
@@ -172,7 +177,7 @@ def measured_traffic(key):
     summary (profiles/dram_traffic.txt: `<path>:<n> <bytes per launch> <kernel rev>`),
     or None when it was taken on other kernel sources."""
     try:
-        rev = kernel_rev()
+        rev = kernel_rev(key.split(":")[0])
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
             for line in f:
                 parts = line.split()
@@ -748,7 +753,7 @@ def run_ours(args):
     # copies in both directions overlapped with the transforms
     # (untimed warm-up calls: the first host transfers after an idle spell run
     # several times slower while the host link ramps up)
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = min(max(args.steps, 10), 20)  # isolated slow host transfers weigh less over more steps
     e2e_warm = max(args.warmup, 6)  # the first host transfers after an idle spell ramp up slowly
     for _ in range(e2e_warm):
         fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)

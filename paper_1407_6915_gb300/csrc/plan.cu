@@ -535,6 +535,9 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             return FFTSEG_OK;
         }
         case PATH_FOURSTEP: {
+            // a batch smaller than a chunk runs as one chunk of its own size, so
+            // that the persistent kernels do no work for absent segments
+            const int cs = (int)(nseg < p->ring_cs ? nseg : p->ring_cs);
             // the producer/consumer kernel stores row tiles with TMA: a box row must
             // hold at least 16 bytes (not so for 2-point-wide power tiles at 2^24)
             const bool ws = p->precision == FFTSEG_PREC_FP32 && (p->flags & FFTSEG_FLAG_FOURSTEP_PRODUCER) &&
@@ -543,7 +546,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 FourStepWsArgs a{};
                 const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
                 const uint32_t boxa = (uint32_t)(n1 < 256 ? n1 : 256), boxb = (uint32_t)(n2 < 256 ? n2 : 256);
-                const int64_t slabs = (int64_t)p->ring_nr * p->ring_cs;
+                const int64_t slabs = (int64_t)p->ring_nr * cs;
                 const int esz = power ? 4 : 8;
                 int rc = encode_tmap_3d(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, 1u << p->log_wa, boxa);
                 if (rc == FFTSEG_OK)
@@ -553,7 +556,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 if (rc == FFTSEG_OK)
                     rc = encode_tmap_3d(&a.tmO, d_out, n1, n2, nseg, n1 * esz, n * esz, 1u << p->log_wb, boxb, esz);
                 if (rc != FFTSEG_OK) return rc;
-                const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+                const int64_t nc = (nseg + cs - 1) / cs;
                 a.ring = p->ring;
                 a.twA = p->twA;
                 a.twB = p->twB;
@@ -563,7 +566,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 a.err = p->d_err;
                 a.nseg = nseg;
                 a.nchunks = (int)nc;
-                a.cs = p->ring_cs;
+                a.cs = cs;
                 a.nr = p->ring_nr;
                 a.out_power = power;
                 a.scale = p->scale;
@@ -577,12 +580,12 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             if (uses_fourstep_hw(p)) {
                 // n = 256 x 256: warp-local lines, loader and retirer warps, TMA output stores
                 FourStepHwArgs a{};
-                const int64_t slabs = (int64_t)p->ring_nr * p->ring_cs;
+                const int64_t slabs = (int64_t)p->ring_nr * cs;
                 int rc = encode_tmap_3d(&a.tmA, in, 256, 256, nseg, 256 * 8, n * 8, 16, 256, 8, true);
                 if (rc == FFTSEG_OK) rc = encode_tmap_3d(&a.tmB, p->ring, 256, 256, slabs, 256 * 8, n * 8, 16, 256, 8, true);
                 if (rc == FFTSEG_OK) rc = encode_tmap_3d(&a.tmO, d_out, 256, 256, nseg, 256 * 8, n * 8, 16, 256, 8, true);
                 if (rc != FFTSEG_OK) return rc;
-                const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+                const int64_t nc = (nseg + cs - 1) / cs;
                 a.ring = p->ring;
                 a.twL = p->twA;
                 a.w4t = p->w4t;
@@ -590,9 +593,9 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 a.err = p->d_err;
                 a.nseg = nseg;
                 a.nchunks = (int)nc;
-                a.cs = p->ring_cs;
+                a.cs = cs;
                 a.nr = p->ring_nr;
-                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * p->ring_cs) * sizeof(int), st);
+                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
                 e = launch_fourstep_hw(sign, a, st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
@@ -604,10 +607,10 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             const uint32_t boxa = (uint32_t)(n1 < 256 ? n1 : 256), boxb = (uint32_t)(n2 < 256 ? n2 : 256);
             int rc = encode_tmap_3d(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, 1u << p->log_wa, boxa);
             if (rc != FFTSEG_OK) return rc;
-            rc = encode_tmap_3d(&a.tmB, p->ring, n1, n2, (int64_t)p->ring_nr * p->ring_cs, n1 * 8, n * 8,
+            rc = encode_tmap_3d(&a.tmB, p->ring, n1, n2, (int64_t)p->ring_nr * cs, n1 * 8, n * 8,
                                 1u << p->log_wb, boxb);
             if (rc != FFTSEG_OK) return rc;
-            const int64_t nc = (nseg + p->ring_cs - 1) / p->ring_cs;
+            const int64_t nc = (nseg + cs - 1) / cs;
             a.out = d_out;
             a.ring = p->ring;
             a.twA = p->twA;
@@ -618,7 +621,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             a.err = p->d_err;
             a.nseg = nseg;
             a.nchunks = (int)nc;
-            a.cs = p->ring_cs;
+            a.cs = cs;
             a.nr = p->ring_nr;
             a.log_k = p->w4_log_k;
             a.out_power = power;
@@ -749,6 +752,10 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
 // reduced exactly as (m^2 mod 2n) / n, and b = conj(w) placed cyclically and
 // divided by M (exact) are evaluated in double on the host; B = FFT_M(b) is
 // computed once on the device with the plan's own forward M-point plan.
+// Bluestein rows go through five passes: larger chunks than for the real and
+// frame paths, so that launches do not dominate at small n.
+constexpr int64_t kBlueChunkBytes = 256ll << 20;
+
 int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int out_kind,
                      unsigned flags)
 {
@@ -774,7 +781,7 @@ int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, 
     p->bm = M;
     if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
     else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
-    int64_t cs = kRealChunkBytes / (M * 8);
+    int64_t cs = kBlueChunkBytes / (M * 8);
     if (cs < 1) cs = 1;
     if (cs > 65535) cs = 65535;
     if (cs > batch) cs = batch;
