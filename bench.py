@@ -627,6 +627,18 @@ def serve_bench(peak, njobs=600, seed=5):
             "saturated_hbm_frac": round(16.0 * samples / wall_sat / 1e9 / peak, 4), "loads": loads}
 
 
+def max_over_ranks(value, device=None):
+    """The largest of every rank's value, on every rank (the job's time is its
+    slowest rank's); the value itself in a single process."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -729,11 +741,7 @@ def run_ours(args):
     launches = fs.launch_count() - launches0
     ms = e_start.elapsed_time(e_end)
     kernel_ms = [a.elapsed_time(b) for a, b, _ in evs] + [b.elapsed_time(c) for _, b, c in evs]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev)
     ms_per_step = ms / args.steps
     flops_step = 2 * flops_per_transform(N, S)
     value = world * flops_step / (ms_per_step / 1e3) / 1e9

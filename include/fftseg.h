@@ -178,21 +178,31 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
  * File-backed streaming: the paper's pipeline end to end on one GPU (Sec. III,
  * a signal file cut into segments, each transformed, the results written in
  * positional order).  fftseg_stream with a reader and a writer over files:
- *   in_path     the complex64 signal; its size is the signal length
+ *   in_path     the complex64 signal
  *   out_path    receives the results at output offset s*n*8 (complex) or
- *               s*n*4 (power); created, or truncated when start_offset is 0
- *               (a resumed run keeps what lies before its start)
- *   start_offset, chunk_segments, committed_offset  as for fftseg_stream
- *   direct      non-zero: O_DIRECT reads and writes (the page cache bypassed)
- *               where segment sizes are multiples of 4096 bytes and the file
- *               system allows it; buffered I/O otherwise
+ *               s*n*4 (power); created, and truncated when start_offset is 0
+ *               unless FFTSEG_FILE_KEEP (a resumed run keeps what lies before
+ *               its start)
+ *   start_offset, end_offset  the input byte range [start, end) to transform;
+ *               end_offset 0 (or past the end) means the end of the file;
+ *               start_offset a multiple of n*8.  Several processes can each
+ *               take a range of the same file and write the same output
+ *               (FFTSEG_FILE_KEEP): the results land at their positions with
+ *               no merge step.
+ *   chunk_segments, committed_offset  as for fftseg_stream
+ *   file_flags  FFTSEG_FILE_DIRECT: O_DIRECT reads and writes (the page cache
+ *               bypassed) where segment sizes are multiples of 4096 bytes and
+ *               the file system allows it, buffered I/O otherwise;
+ *               FFTSEG_FILE_KEEP: never truncate the output
  * Synchronous.  FFTSEG_E_IO if a file cannot be opened, read or written; the
  * other results as for fftseg_stream.  The phase split of the run (file reads
  * and writes against transfers and transforms, the analog of the paper's I/O
  * versus FFT breakdown, Sec. IV) is in fftseg_stream_phases.
  */
+#define FFTSEG_FILE_DIRECT 0x1u
+#define FFTSEG_FILE_KEEP 0x2u
 int fftseg_stream_file(fftseg_plan p, const char *in_path, const char *out_path, int64_t start_offset,
-                       int64_t chunk_segments, int direct, int64_t *committed_offset);
+                       int64_t end_offset, int64_t chunk_segments, unsigned file_flags, int64_t *committed_offset);
 
 /* Phase split of the last fftseg_stream call on this plan, in milliseconds
  * (the analog of the paper's I/O versus FFT breakdown, Sec. IV Figs. 4-5):

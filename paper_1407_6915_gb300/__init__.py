@@ -24,6 +24,7 @@ OUT_COMPLEX, OUT_POWER = 0, 1
 FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2, FLAG_FOURSTEP_PRODUCER = 0x1, 0x2, 0x4, 0x8
 FLAG_AUTOTUNE = 0x10
 FLAG_REAL = 0x20
+FILE_DIRECT, FILE_KEEP = 0x1, 0x2
 
 
 WINDOW_RECT, WINDOW_HANN = 0, 1
@@ -77,7 +78,8 @@ _SIGS = {
                                      ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "fftseg_stream_file": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64,
-                                          ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_uint,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_autotune": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_double)]),
     "fftseg_exec_host": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p,
@@ -247,13 +249,16 @@ class Plan:
             check(rc, "fftseg_stream")
         return rc, committed.value
 
-    def stream_file(self, in_path, out_path, start_offset=0, chunk_segments=0, direct=True):
-        """fftseg_stream_file: the signal file through the plan into out_path in
+    def stream_file(self, in_path, out_path, start_offset=0, chunk_segments=0, direct=True, end_offset=0,
+                    keep_output=False):
+        """fftseg_stream_file: the input byte range [start_offset, end_offset)
+        (0: to the end) of the signal file through the plan into out_path, in
         positional order.  Returns (status, committed_offset) and does not raise
         on E_IO/E_PARTIAL."""
         committed = ctypes.c_int64(0)
+        flags = (FILE_DIRECT if direct else 0) | (FILE_KEEP if keep_output else 0)
         rc = lib().fftseg_stream_file(self._h, os.fsencode(in_path), os.fsencode(out_path), int(start_offset),
-                                      int(chunk_segments), 1 if direct else 0, ctypes.byref(committed))
+                                      int(end_offset), int(chunk_segments), flags, ctypes.byref(committed))
         if rc not in (OK, E_IO, E_PARTIAL):
             check(rc, "fftseg_stream_file")
         return rc, committed.value

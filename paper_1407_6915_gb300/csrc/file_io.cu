@@ -84,8 +84,10 @@ int open_maybe_direct(const char *path, int flags, bool direct, bool *got_direct
 using namespace fftseg;
 
 extern "C" int fftseg_stream_file(fftseg_plan p, const char *in_path, const char *out_path, int64_t start_offset,
-                                  int64_t chunk_segments, int direct, int64_t *committed_offset)
+                                  int64_t end_offset, int64_t chunk_segments, unsigned file_flags,
+                                  int64_t *committed_offset)
 {
+    const bool direct = (file_flags & FFTSEG_FILE_DIRECT) != 0;
     if (committed_offset) *committed_offset = start_offset;
     if (!p || !in_path || !out_path) return set_error(FFTSEG_E_INVALID, "stream_file: NULL plan or path");
     const int64_t seg_in = p->n * 8, seg_out = p->n * (p->out_kind == FFTSEG_OUT_POWER ? 4 : 8);
@@ -99,16 +101,22 @@ extern "C" int fftseg_stream_file(fftseg_plan p, const char *in_path, const char
         close(in.fd);
         return set_error(FFTSEG_E_IO, "stream_file: cannot stat %s (errno %d)", in_path, errno);
     }
-    // a fresh run replaces the output; a resumed run keeps what is before its start
-    out.fd = open_maybe_direct(out_path, O_WRONLY | O_CREAT | (start_offset == 0 ? O_TRUNC : 0), want_direct,
-                               &out_direct);
+    if (end_offset < 0) {
+        close(in.fd);
+        return set_error(FFTSEG_E_INVALID, "stream_file: end_offset < 0");
+    }
+    const int64_t total = end_offset == 0 || end_offset > (int64_t)st.st_size ? (int64_t)st.st_size : end_offset;
+    // a fresh run replaces the output; a resumed run, or one of several ranks
+    // writing their parts (FFTSEG_FILE_KEEP), keeps what is there
+    const bool trunc = start_offset == 0 && !(file_flags & FFTSEG_FILE_KEEP);
+    out.fd = open_maybe_direct(out_path, O_WRONLY | O_CREAT | (trunc ? O_TRUNC : 0), want_direct, &out_direct);
     if (out.fd < 0) {
         close(in.fd);
         return set_error(FFTSEG_E_IO, "stream_file: cannot open %s (errno %d)", out_path, errno);
     }
     in.direct = in_direct;
     out.direct = out_direct;
-    int rc = fftseg_stream(p, file_read, &in, file_write, &out, (int64_t)st.st_size, start_offset, chunk_segments,
+    int rc = fftseg_stream(p, file_read, &in, file_write, &out, total, start_offset, chunk_segments,
                            committed_offset);
     close(in.fd);
     if (close(out.fd) != 0 && (rc == FFTSEG_OK || rc == FFTSEG_E_PARTIAL))

@@ -83,7 +83,7 @@ def test_null_arguments_are_errors_not_crashes():
 def test_binding_constants_match_the_header():
     text = open(os.path.join(ROOT, "include", "fftseg.h")).read()
     defines = {m.group(1): int(m.group(2), 16) for m in
-               re.finditer(r"#define\s+FFTSEG_(FLAG_\w+)\s+(0x[0-9a-fA-F]+)u", text)}
+               re.finditer(r"#define\s+FFTSEG_((?:FLAG|FILE)_\w+)\s+(0x[0-9a-fA-F]+)u", text)}
     assert defines, "no flag defines found"
     for name, value in defines.items():
         assert getattr(fs, name) == value, name

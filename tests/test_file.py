@@ -82,3 +82,28 @@ def test_file_stream_errors(tmp_path):
     got = np.fromfile(tmp_path / "t.out", dtype=np.complex64)
     assert got.size == 5 * n
     np.testing.assert_array_equal(got, resident(x[: 5 * n], n, fs.OUT_COMPLEX))
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_file_stream_ranges_assemble_the_output(tmp_path, world):
+    # the sharded stream's per-rank calls, one after another in one process:
+    # each writes its segment range [first, last) at its own output offsets
+    from paper_1407_6915_gb300.shard import segment_range, stream_file_sharded
+    n, B, chunk = 4096, 23, 4
+    x = siggen.tones(991, B * n)
+    src, dst = tmp_path / "signal.c64", tmp_path / "spectra.out"
+    x.tofile(src)
+    ref = resident(x, n, fs.OUT_COMPLEX)
+    np.zeros(B * n, dtype=np.complex64).tofile(dst)  # stale content must be overwritten, not truncated
+    plan = fs.Plan(n, chunk, fs.FORWARD)
+    for r in reversed(range(world)):  # any order: each range lands at its offsets
+        first, last = segment_range(B, r, world)
+        rc, committed = plan.stream_file(src, dst, start_offset=first * n * 8, end_offset=last * n * 8,
+                                         chunk_segments=chunk, keep_output=True)
+        assert rc == fs.OK and committed == last * n * 8
+    np.testing.assert_array_equal(np.fromfile(dst, dtype=np.complex64), ref)
+    # the sharded driver with a no-op barrier, world 1
+    dst2 = tmp_path / "one.out"
+    rc, committed = stream_file_sharded(plan, src, dst2, 0, 1, lambda: None, chunk_segments=chunk)
+    assert rc == fs.OK and committed == B * n * 8
+    np.testing.assert_array_equal(np.fromfile(dst2, dtype=np.complex64), ref)
