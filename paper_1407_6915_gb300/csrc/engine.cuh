@@ -241,6 +241,24 @@ constexpr uint32_t kSpinLimit = 1u << 24;
 
 FDEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// 8-byte asynchronous copy global -> shared (cp.async; any 8-byte-aligned
+// source).  src_bytes = 0 writes zeros and reads nothing.  Copies are grouped
+// by cp_async_commit; cp_async_wait<N> returns once at most N of the calling
+// thread's groups are pending, and the thread then sees its own copies
+// (other threads' copies need a barrier after their waits).
+FDEV void cp_async8(void *smem_dst, const void *gsrc, uint32_t src_bytes)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(smem_dst)), "l"(gsrc),
+                 "r"(src_bytes)
+                 : "memory");
+}
+FDEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+FDEV void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 FDEV void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

@@ -77,6 +77,19 @@ struct FramesArgs {
     int n;
 };
 cudaError_t launch_frames(FramesArgs a, int64_t nframes, cudaStream_t st);
+// Frames of n = 2^log_l <= 4096 points in one fused pass (frames.cu): the
+// windowed frames of the signal straight to their forward bins.
+struct FramesBlockArgs {
+    const float2 *signal;  // frame f starts at signal + f * hop
+    void *out;             // [nframes][n] complex64, or float32 |X|^2
+    const float *window;   // n values, or null for the rectangular window
+    const float2 *twL;     // stage tables of the n-point line
+    int *err;              // set to 1 if a copy never completed
+    int64_t hop, nframes, ntiles;
+    int out_power;
+    float scale;
+};
+cudaError_t launch_block_frames(int log_l, const FramesBlockArgs &a, cudaStream_t st);
 // Lengths that are not powers of two (bluestein.cu): step 0 chirps x into the
 // M-point work rows (zero-padded), step 1 multiplies them by B, step 2 chirps
 // the first n points out into d_out ([nseg][n], complex64 or float32 |X|^2,
@@ -91,6 +104,19 @@ struct BlueArgs {
     float scale;
 };
 cudaError_t launch_blue(int step, bool power, const BlueArgs &a, int64_t nseg, cudaStream_t st);
+// Bluestein rows with M = 2^log_m <= 4096 in one fused pass (bluestein.cu).
+struct BlueBlockArgs {
+    const float2 *x;     // [nseg][n]
+    void *out;           // [nseg][n] complex64, or float32 |X|^2
+    const float2 *w;     // chirp, n values
+    const float2 *bhat;  // FFT_M of the conjugate chirp, divided by M
+    const float2 *twL;   // stage tables of the M-point line
+    int *err;            // set to 1 if a copy never completed
+    int64_t n, nseg, ntiles;
+    int out_power;
+    float scale;
+};
+cudaError_t launch_blue_block(int log_m, const BlueBlockArgs &a, cudaStream_t st);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

@@ -35,6 +35,19 @@ bool uses_fourstep_hw(const fftseg_plan_s *p)
     return p->log_n == 16 && p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
            !(p->flags & FFTSEG_FLAG_FOURSTEP_PRODUCER);
 }
+// Bluestein plans whose M-point rows fit one block tile (M <= 4096, the
+// inner forward plan on the block path) run as one fused kernel.
+bool blue_fused(const fftseg_plan_s *p)
+{
+    return p->bm <= 4096 && p->inner && p->inner->path == PATH_BLOCK && p->inner->precision == FFTSEG_PREC_FP32;
+}
+// Frame plans of n <= 4096 points (the inner plan on the block path) run as
+// one fused kernel.
+bool frames_fused(const fftseg_plan_s *p)
+{
+    return p->path == PATH_FRAMES && p->inner && p->inner->path == PATH_BLOCK &&
+           p->inner->precision == FFTSEG_PREC_FP32;
+}
 int ilog2(int64_t n)
 {
     int l = 0;
@@ -294,6 +307,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
         case PATH_BLUESTEIN: {
+            if (blue_fused(p)) return 1;
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
                 const int64_t c = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
@@ -304,6 +318,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_REAL:
         case PATH_FRAMES: {
             if (p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) return 1;
+            if (frames_fused(p)) return 1;
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
                 k += 1 + launches_per_exec(p->inner, nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk);
@@ -345,6 +360,26 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
+    if (p->path == PATH_BLUESTEIN && blue_fused(p)) {
+        // M <= 4096: every row on chip from chirp-in to chirp-out, one launch
+        BlueBlockArgs a{};
+        const int64_t W = block_segments_per_cta(p->log_n);
+        a.x = static_cast<const float2 *>(d_in);
+        a.out = d_out;
+        a.w = p->bw;
+        a.bhat = p->bhat;
+        a.twL = p->inner->twA;
+        a.err = p->d_err;
+        a.n = p->n;
+        a.nseg = nseg;
+        a.ntiles = (nseg + W - 1) / W;
+        a.out_power = p->out_kind == FFTSEG_OUT_POWER;
+        a.scale = p->scale;
+        cudaError_t e = launch_blue_block(p->log_n, a, st);
+        if (e != cudaSuccess) return cuda_error(e, "Bluestein block kernel launch");
+        count_launches(1);
+        return FFTSEG_OK;
+    }
     if (p->path == PATH_BLUESTEIN) {
         // chunks of rchunk segments: chirp in, M-point forward transform,
         // product with B, M-point inverse transform, chirp out
@@ -372,6 +407,25 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             if (e != cudaSuccess) return cuda_error(e, "chirp-out launch");
             count_launches(3);
         }
+        return FFTSEG_OK;
+    }
+    if (p->path == PATH_FRAMES && frames_fused(p)) {
+        // n <= 4096: windowed frames straight to their bins, one launch
+        FramesBlockArgs a{};
+        const int64_t W = block_segments_per_cta(p->log_n);
+        a.signal = static_cast<const float2 *>(d_in);
+        a.out = d_out;
+        a.window = p->fwin;
+        a.twL = p->inner->twA;
+        a.err = p->d_err;
+        a.hop = p->hop;
+        a.nframes = nseg;
+        a.ntiles = (nseg + W - 1) / W;
+        a.out_power = p->out_kind == FFTSEG_OUT_POWER;
+        a.scale = p->inner->scale;
+        cudaError_t e = launch_block_frames(p->log_n, a, st);
+        if (e != cudaSuccess) return cuda_error(e, "frames block kernel launch");
+        count_launches(1);
         return FFTSEG_OK;
     }
     if (p->path == PATH_FRAMES) {
@@ -734,7 +788,8 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
         if (e != cudaSuccess) rc = cuda_error(e, "window table");
     }
     if (rc == FFTSEG_OK) {
-        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * n) * sizeof(float2));
+        // fused frames (n <= 4096) need no intermediate
+        e = frames_fused(p) ? cudaSuccess : cudaMalloc((void **)&p->rwork, (size_t)(cs * n) * sizeof(float2));
         if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(frames intermediate)");
@@ -788,7 +843,10 @@ int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, 
     p->rchunk = cs;
     int rc = fftseg_plan_create(&p->inner, M, cs, FFTSEG_FORWARD, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
                                 FFTSEG_OUT_COMPLEX, flags);
-    if (rc == FFTSEG_OK)
+    // M <= 4096 rows run fused (k_blue_block) on the inner plan's stage
+    // tables: no inverse plan and no intermediate rows
+    const bool fused = rc == FFTSEG_OK && blue_fused(p);
+    if (rc == FFTSEG_OK && !fused)
         rc = fftseg_plan_create(&p->inner2, M, cs, FFTSEG_INVERSE, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
                                 FFTSEG_OUT_COMPLEX, flags);
     if (rc == FFTSEG_OK) {
@@ -816,7 +874,7 @@ int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, 
         cudaFree(bdev);
     }
     if (rc == FFTSEG_OK) {
-        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
+        e = fused ? cudaSuccess : cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
         if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(Bluestein rows)");
@@ -972,8 +1030,8 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
                p->path == PATH_BLUESTEIN)
                   ? 1
                   : int64_t(1) << p->log_n2;
-    info[3] = p->path == PATH_BLUESTEIN ? p->rchunk * p->bm * 8
-              : p->path == PATH_FRAMES ? p->rchunk * p->n * 8
+    info[3] = p->path == PATH_BLUESTEIN ? (p->rwork ? p->rchunk * p->bm * 8 : 0)
+              : p->path == PATH_FRAMES ? (p->rwork ? p->rchunk * p->n * 8 : 0)
               : p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
                                     : p->work ? p->work_segs * p->n * 8
                                               : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);

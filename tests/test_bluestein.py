@@ -94,3 +94,26 @@ def test_bluestein_power_and_stream():
     rc, committed = sp.stream(rd, None, wr, None, x.nbytes, 0, 16)
     assert rc == fs.OK and committed == x.nbytes and len(chunks) == 3
     np.testing.assert_array_equal(out.reshape(B, n), got)
+
+
+@pytest.mark.parametrize("n,B,out_kind", [(3, 1000, fs.OUT_COMPLEX), (100, 37, fs.OUT_POWER),
+                                          (1000, 131, fs.OUT_COMPLEX), (2047, 3, fs.OUT_POWER),
+                                          (2049, 3, fs.OUT_COMPLEX)])
+def test_bluestein_fused_rows(n, B, out_kind):
+    # rows with M <= 4096 run in one fused launch with no intermediate rows
+    # (ragged last tiles: B is no multiple of 4096 / M); M = 8192 (n = 2049)
+    # goes through the five-pass chunks
+    M = 1 << math.ceil(math.log2(2 * n - 1))
+    x = siggen.tones(1600 + n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, fs.INVERSE, fs.NORM_ORTHO, out_kind=out_kind)
+    info = plan.info()
+    if M <= 4096:
+        assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0
+    else:
+        assert info["launches_per_exec"] > 1 and info["work_bytes"] > 0
+    got = run(plan, x)
+    X = oracle.dft(x, fs.INVERSE, fs.NORM_ORTHO)
+    if out_kind == fs.OUT_POWER:
+        assert rel_l2(got, X.real ** 2 + X.imag ** 2) <= 2 * tol_blue(n)
+    else:
+        assert rel_l2(got, X) <= tol_blue(n)

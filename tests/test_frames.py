@@ -82,3 +82,36 @@ def test_frame_plan_rejections():
     except fs.FFTSegError as e:
         rc_stream = e.status
     assert rc_stream == fs.E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("log_n,hop,F", [(1, 1, 1000), (2, 3, 777), (5, 7, 300), (9, 256, 51), (12, 4095, 5),
+                                         (13, 4096, 5)])
+def test_fused_frames(log_n, hop, F):
+    # frames of n <= 4096 points run in one launch with no intermediate
+    # (ragged last tiles: F is no multiple of 4096 / n); n = 8192 is chunked
+    n = 1 << log_n
+    x = signal(90 + log_n, (F - 1) * hop + n)
+    plan = fs.FramePlan(n, hop, F, fs.WINDOW_HANN, norm=fs.NORM_BACKWARD)
+    info = plan.info()
+    if n <= 4096:
+        assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0
+    else:
+        assert info["launches_per_exec"] > 1 and info["work_bytes"] > 0
+    got = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    X = oracle.frames_fft(x, n, hop, F, oracle.WINDOW_HANN, oracle.NORM_BACKWARD)
+    assert rel_l2(got.cpu().numpy().astype(np.complex128), X) <= tol_fp32(max(n, 2))
+
+
+def test_frames_signal_off_16_bytes_is_rejected():
+    # device buffers are 16-byte aligned by contract (the bulk copies rely on
+    # it); a signal 8 bytes past a boundary is refused, not read
+    n, hop, F = 1024, 512, 4
+    x = signal(99, (F - 1) * hop + n + 1)
+    xd = torch.from_numpy(x).cuda()[1:]
+    assert xd.data_ptr() % 16 == 8
+    plan = fs.FramePlan(n, hop, F, fs.WINDOW_HANN)
+    with pytest.raises(fs.FFTSegError) as e:
+        plan.exec(xd)
+    assert e.value.status == fs.E_INVALID
