@@ -80,8 +80,9 @@ enum { FFTSEG_WINDOW_RECT = 0, FFTSEG_WINDOW_HANN = 1 };
    float32 |X|^2); an inverse plan takes [batch][n/2 + 1] complex64 bins and
    writes [batch][n] float32 samples of the inverse DFT of their Hermitian
    extension (the imaginary parts of X[0] and X[n/2] are ignored).  n is a power
-   of two in [4, 2^24]; FP32 only; out of place only; not for fftseg_stream,
-   fftseg_exec_host or the server.  Scaling as for complex plans, with n the
+   of two in [4, 2^24]; FP32 only; out of place only; streamed by fftseg_stream
+   (4n input bytes per forward segment); not for fftseg_exec_host or the
+   server.  Scaling as for complex plans, with n the
    real length.  Runs as a complex FFT of n/2 points on the samples read as
    complex values, plus one pass that splits (forward) or joins (inverse) the
    spectra of the even and odd samples, in chunks whose intermediate stays in L2. */
@@ -143,9 +144,10 @@ int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg,
  * Run it with fftseg_exec / fftseg_exec_n: d_in is the complex64 signal and must
  * hold at least (nframes - 1)*hop + n samples (the library cannot check the
  * size of a device buffer); d_out is [nframes][n] complex64 (or float32 |X|^2);
- * out of place only.  Frames are windowed into an intermediate of at most
- * 32 MiB, which then goes through the n-point transform.  Not for fftseg_stream,
- * fftseg_exec_host or the server.
+ * out of place only.  Frames of n <= 4096 points go from the signal to their
+ * bins in one pass; longer frames are windowed into an intermediate of at most
+ * 32 MiB, which then goes through the n-point transform.  fftseg_stream takes
+ * frame plans (see there); fftseg_exec_host and the server do not.
  */
 int fftseg_plan_create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t batch, int norm,
                               int out_kind, unsigned flags);
@@ -167,6 +169,18 @@ int fftseg_plan_create_frames(fftseg_plan *out, int64_t n, int64_t hop, int wind
  * Synchronous.  Returns FFTSEG_E_IO on a callback error, FFTSEG_E_PARTIAL if
  * the signal ends inside a segment without FFTSEG_FLAG_ZERO_PAD (the complete
  * segments before it are written).
+ * Real-signal plans (FFTSEG_FLAG_REAL): a segment is 4n bytes of float32
+ * samples in and (n/2 + 1) bins out (forward), or the reverse (inverse);
+ * offsets and start_offset count those bytes.
+ * Frame plans (fftseg_plan_create_frames): the signal is complex64 samples
+ * (total_bytes a multiple of 8); chunk_segments counts frames; every frame
+ * that lies wholly inside the signal is transformed (trailing samples that
+ * start no complete frame are not an error) and frame f's bins go to output
+ * offset f*n*8 (or f*n*4).  Consecutive chunks share n - hop samples, which
+ * are carried over rather than read again, so each sample is read once when
+ * hop <= n.  start_offset must be f*hop*8 for a frame f, and committed_offset
+ * receives f*hop*8 for the first frame whose bins were not written.  A short
+ * read ends the signal after the frames that fit in it.
  */
 typedef int64_t (*fftseg_read_fn)(void *ctx, int64_t byte_offset, void *dst, int64_t bytes);
 typedef int (*fftseg_write_fn)(void *ctx, int64_t byte_offset, const void *src, int64_t bytes);
@@ -178,9 +192,11 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
  * File-backed streaming: the paper's pipeline end to end on one GPU (Sec. III,
  * a signal file cut into segments, each transformed, the results written in
  * positional order).  fftseg_stream with a reader and a writer over files:
- *   in_path     the complex64 signal
- *   out_path    receives the results at output offset s*n*8 (complex) or
- *               s*n*4 (power); created, and truncated when start_offset is 0
+ *   in_path     the signal (complex64; float32 samples or bins for a
+ *               real-signal plan; frames for a frame plan, as fftseg_stream
+ *               describes)
+ *   out_path    receives the results at the output offsets of fftseg_stream
+ *               (s*n*8 complex, s*n*4 power); created, and truncated when start_offset is 0
  *               unless FFTSEG_FILE_KEEP (a resumed run keeps what lies before
  *               its start)
  *   start_offset, end_offset  the input byte range [start, end) to transform;
@@ -192,7 +208,8 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
  *   chunk_segments, committed_offset  as for fftseg_stream
  *   file_flags  FFTSEG_FILE_DIRECT: O_DIRECT reads and writes (the page cache
  *               bypassed) where segment sizes are multiples of 4096 bytes and
- *               the file system allows it, buffered I/O otherwise;
+ *               the file system allows it (never for frame plans, which read
+ *               at frame offsets), buffered I/O otherwise;
  *               FFTSEG_FILE_KEEP: never truncate the output
  * Synchronous.  FFTSEG_E_IO if a file cannot be opened, read or written; the
  * other results as for fftseg_stream.  The phase split of the run (file reads

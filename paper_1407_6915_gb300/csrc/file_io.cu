@@ -90,8 +90,11 @@ extern "C" int fftseg_stream_file(fftseg_plan p, const char *in_path, const char
     const bool direct = (file_flags & FFTSEG_FILE_DIRECT) != 0;
     if (committed_offset) *committed_offset = start_offset;
     if (!p || !in_path || !out_path) return set_error(FFTSEG_E_INVALID, "stream_file: NULL plan or path");
-    const int64_t seg_in = p->n * 8, seg_out = p->n * (p->out_kind == FFTSEG_OUT_POWER ? 4 : 8);
-    const bool want_direct = direct && seg_in % kDirectAlign == 0 && seg_out % kDirectAlign == 0;
+    int64_t seg_in = 0, seg_out = 0;
+    segment_bytes(p, &seg_in, &seg_out);
+    // frame plans read at frame offsets (multiples of hop), so they use the page cache
+    const bool want_direct =
+        direct && p->path != PATH_FRAMES && seg_in % kDirectAlign == 0 && seg_out % kDirectAlign == 0;
     FileCtx in, out;
     bool in_direct = false, out_direct = false;
     in.fd = open_maybe_direct(in_path, O_RDONLY, want_direct, &in_direct);

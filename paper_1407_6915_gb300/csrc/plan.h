@@ -99,6 +99,9 @@ int tune_schedule(int64_t n, int64_t batch, int prec, int out_kind, unsigned *fl
 
 // Run the plan on nseg segments (arguments already validated).
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st);
+// Bytes of one segment's input and output in fftseg_stream (complex plans of
+// any length and real-signal plans).
+void segment_bytes(const fftseg_plan_s *p, int64_t *in, int64_t *out);
 
 // Forward-direction roots of unity w_M^m for m < M, evaluated in double.
 void host_roots(float2 *t, int64_t count, int64_t M, int64_t stride_exp);

@@ -76,12 +76,11 @@ def test_frame_plan_rejections():
         plan.exec_ptr(buf.data_ptr(), buf.data_ptr(), 3)  # out of place only
     with pytest.raises(ValueError):
         plan.exec(torch.zeros(1000, dtype=torch.complex64, device="cuda"), nseg=1)  # not one whole frame
-    rc_stream = None
-    try:
-        plan.stream(lambda *a: 0, None, lambda *a: 0, None, 8192)
-    except fs.FFTSegError as e:
-        rc_stream = e.status
-    assert rc_stream == fs.E_UNSUPPORTED
+    for total, start in [(8196, 0), (8192, 8), (8192, 4096 * 8 * 2)]:
+        # a partial sample; a start that is not a frame's first sample; a start past the last frame
+        with pytest.raises(fs.FFTSegError) as e:
+            plan.stream(lambda *a: 0, None, lambda *a: 0, None, total, start)
+        assert e.value.status == fs.E_INVALID
 
 
 @pytest.mark.parametrize("log_n,hop,F", [(1, 1, 1000), (2, 3, 777), (5, 7, 300), (9, 256, 51), (12, 4095, 5),
