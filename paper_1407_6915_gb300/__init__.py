@@ -187,6 +187,18 @@ class Plan:
     def handle(self):
         return self._h.value
 
+    def segment_bytes(self):
+        """(input, output) bytes of one segment as fftseg_stream counts them:
+        complex64 n points in, n complex64 or float32 |X|^2 out; real-signal
+        plans take 4n bytes of samples (forward) or n/2 + 1 bins (inverse)."""
+        pw = 4 if self.out_kind == OUT_POWER else 8
+        if self.flags & FLAG_REAL:
+            bins = (self.n // 2 + 1) * 8
+            if self.direction == FORWARD:
+                return self.n * 4, (self.n // 2 + 1) * pw
+            return bins, self.n * 4
+        return self.n * 8, self.n * pw
+
     def info(self) -> dict:
         a = (ctypes.c_int64 * 6)()
         check(lib().fftseg_plan_info(self._h, a), "fftseg_plan_info")

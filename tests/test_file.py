@@ -107,3 +107,36 @@ def test_file_stream_ranges_assemble_the_output(tmp_path, world):
     rc, committed = stream_file_sharded(plan, src, dst2, 0, 1, lambda: None, chunk_segments=chunk)
     assert rc == fs.OK and committed == B * n * 8
     np.testing.assert_array_equal(np.fromfile(dst2, dtype=np.complex64), ref)
+
+
+def test_file_stream_frames_real_and_sharded_ranges(tmp_path):
+    # a frame plan through the file stream equals the resident frame plan,
+    # whole and as two frame ranges (the sharded driver's calls, in order)
+    from paper_1407_6915_gb300.shard import stream_file_sharded
+    n, hop, F = 1024, 384, 150
+    x = siggen.tones(995, (F - 1) * hop + n + 100)  # 100 samples start no frame
+    src = tmp_path / "signal.c64"
+    x.tofile(src)
+    ref = fs.FramePlan(n, hop, F, fs.WINDOW_HANN).exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    ref = ref.cpu().numpy()
+    plan = fs.FramePlan(n, hop, 32, fs.WINDOW_HANN)
+    rc, committed = plan.stream_file(src, tmp_path / "frames.out", chunk_segments=32)
+    assert rc == fs.OK and committed == F * hop * 8
+    np.testing.assert_array_equal(np.fromfile(tmp_path / "frames.out", dtype=np.complex64).reshape(F, n), ref)
+    for r in range(2):
+        rc, _ = stream_file_sharded(plan, src, tmp_path / "frames2.out", r, 2, lambda: None, chunk_segments=32)
+        assert rc == fs.OK
+    np.testing.assert_array_equal(np.fromfile(tmp_path / "frames2.out", dtype=np.complex64).reshape(F, n), ref)
+    # a real-signal plan: 4n bytes of float32 samples per segment in
+    n, B = 4096, 50
+    xr = siggen.tones(996, B * n // 2).view(np.float32).reshape(B, n)
+    xr.tofile(tmp_path / "real.f32")
+    rplan = fs.Plan(n, B, fs.FORWARD, flags=fs.FLAG_REAL)
+    rref = rplan.exec(torch.from_numpy(xr).cuda())
+    torch.cuda.synchronize()
+    sp = fs.Plan(n, 16, fs.FORWARD, flags=fs.FLAG_REAL)
+    rc, committed = sp.stream_file(tmp_path / "real.f32", tmp_path / "real.out", chunk_segments=16)
+    assert rc == fs.OK and committed == xr.nbytes
+    got = np.fromfile(tmp_path / "real.out", dtype=np.complex64).reshape(B, n // 2 + 1)
+    np.testing.assert_array_equal(got, rref.cpu().numpy())

@@ -42,6 +42,9 @@ class FilePlan:
     def __init__(self, n):
         self.n = n
 
+    def segment_bytes(self):
+        return self.n * 8, self.n * 8
+
     def stream_file(self, in_path, out_path, start_offset=0, end_offset=0, chunk_segments=0, direct=True,
                     keep_output=False):
         assert keep_output and start_offset % (self.n * 8) == 0
@@ -56,19 +59,43 @@ class FilePlan:
         return 0, end_offset
 
 
+class FrameFilePlan:
+    """The same for a frame plan: frame f (samples [f*hop, f*hop + n)) goes,
+    negated, to output offset f*n*8; the input range [start, end) holds the
+    frames that lie wholly inside it."""
+
+    def __init__(self, n, hop):
+        self.n, self.hop = n, hop
+
+    def stream_file(self, in_path, out_path, start_offset=0, end_offset=0, chunk_segments=0, direct=True,
+                    keep_output=False):
+        assert keep_output and start_offset % (self.hop * 8) == 0
+        if end_offset == 0:
+            end_offset = os.path.getsize(in_path)
+        x = np.fromfile(in_path, dtype=np.complex64)[start_offset // 8: end_offset // 8]
+        f0 = start_offset // (self.hop * 8)
+        nf = 0 if x.size < self.n else (x.size - self.n) // self.hop + 1
+        with open(out_path, "r+b") as f:
+            for k in range(nf):
+                f.seek((f0 + k) * self.n * 8)
+                f.write((-x[k * self.hop: k * self.hop + self.n]).tobytes())
+        return 0, (f0 + nf) * self.hop * 8
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, in_path, out_path, n, results):
+def _worker(rank, world, port, in_path, out_path, n, results, hop=None):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
     dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=60))
     try:
-        rc, committed = stream_file_sharded(FilePlan(n), in_path, out_path, rank, world, dist.barrier)
+        plan = FilePlan(n) if hop is None else FrameFilePlan(n, hop)
+        rc, committed = stream_file_sharded(plan, in_path, out_path, rank, world, dist.barrier)
         import bench
         slowest = bench.max_over_ranks(1.5 + rank)
         results[rank] = (rc, committed, slowest)
@@ -92,3 +119,23 @@ def test_sharded_file_stream_and_max_over_ranks_with_gloo(tmp_path):
         rc, committed, slowest = results[r]
         assert rc == 0 and committed == segment_range(nseg, r, world)[1] * n * 8
         assert slowest == 1.5 + world - 1  # the max over ranks, on every rank
+
+
+def test_sharded_frames_with_gloo(tmp_path):
+    # frames split over ranks by frame ranges: each rank reads from its first
+    # frame's start to its last frame's end (the overlap read by both sides)
+    import torch.multiprocessing as mp
+    n, hop, world = 64, 24, 2
+    F = 37
+    x = (np.arange((F - 1) * hop + n + 5) * (1 + 0.5j)).astype(np.complex64)  # 5 samples start no frame
+    src, dst = tmp_path / "signal.c64", tmp_path / "frames.c64"
+    x.tofile(src)
+    with mp.Manager() as mgr:
+        results = mgr.dict()
+        mp.spawn(_worker, args=(world, _free_port(), str(src), str(dst), n, results, hop), nprocs=world, join=True)
+        results = dict(results)
+    ref = -np.stack([x[f * hop: f * hop + n] for f in range(F)]).ravel()
+    np.testing.assert_array_equal(np.fromfile(dst, dtype=np.complex64), ref)
+    for r in range(world):
+        rc, committed, _ = results[r]
+        assert rc == 0 and committed == segment_range(F, r, world)[1] * hop * 8
