@@ -284,8 +284,9 @@ def extra(fn, *args):
     try:
         return fn(*args)
     except Exception as e:  # noqa: BLE001 - reported in the line, not hidden
-        torch.cuda.synchronize()
-        torch.cuda.empty_cache()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
         return {"error": "%s: %s" % (type(e).__name__, e)}
 
 
