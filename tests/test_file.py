@@ -140,3 +140,16 @@ def test_file_stream_frames_real_and_sharded_ranges(tmp_path):
     assert rc == fs.OK and committed == xr.nbytes
     got = np.fromfile(tmp_path / "real.out", dtype=np.complex64).reshape(B, n // 2 + 1)
     np.testing.assert_array_equal(got, rref.cpu().numpy())
+
+
+def test_command_line_job(tmp_path):
+    # python -m paper_1407_6915_gb300: the whole file through one GPU, as the
+    # resident plan would transform it
+    from paper_1407_6915_gb300 import __main__ as cli
+    n, B = 4096, 40
+    x = siggen.tones(997, B * n)
+    x.tofile(tmp_path / "in.c64")
+    rc = cli.main([str(tmp_path / "in.c64"), str(tmp_path / "out.f32"), "--n", str(n), "--power"])
+    assert rc == 0
+    got = np.fromfile(tmp_path / "out.f32", dtype=np.float32)
+    np.testing.assert_array_equal(got, resident(x, n, fs.OUT_POWER))
