@@ -323,6 +323,19 @@ int64_t fftseg_launch_count(void);
 int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int64_t nseg, int direction, int norm,
                         fftseg_stream_t stream);
 
+/* Error check for fftseg_exec_noalloc on the current device, the counterpart
+ * of fftseg_plan_check. The kernels of fftseg_exec_noalloc record a give-up
+ * (a bounded wait that ran out, or a misaligned shared buffer) in a flag kept
+ * in the same fixed array; the flag is not cleared by later calls, so it
+ * covers every call since the last check. This call waits for the device,
+ * reads the flag and clears it: FFTSEG_E_TIMEOUT if it was set (the outputs
+ * of those calls are not valid), FFTSEG_OK otherwise, and FFTSEG_OK if no
+ * call has run on this device. It allocates nothing.
+ * The array's device address and the record of which length's tables it
+ * holds are kept per device for the life of the process: do not use these
+ * two calls on a device after cudaDeviceReset. */
+int fftseg_noalloc_check(void);
+
 /* ---------------------------------------------------------------- serving
  * Continuous batching of segment-FFT jobs of different lengths.  Jobs are
  * admitted in arrival order while the bytes they touch fit the HBM budget and

@@ -86,6 +86,7 @@ _SIGS = {
                                         ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
     "fftseg_exec_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "fftseg_noalloc_check": (ctypes.c_int, []),
     "fftseg_plan_destroy": (ctypes.c_int, [ctypes.c_void_p]),
     "fftseg_plan_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_plan_check": (ctypes.c_int, [ctypes.c_void_p]),

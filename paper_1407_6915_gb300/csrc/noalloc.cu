@@ -182,3 +182,33 @@ extern "C" int fftseg_exec_noalloc(const void *d_in, void *d_out, int64_t n, int
     }
     return FFTSEG_OK;
 }
+
+// Reads and clears the give-up flag that fftseg_exec_noalloc's kernels set on
+// the current device (a slot of the same fixed array): FFTSEG_E_TIMEOUT if any
+// call since the last check gave up a bounded wait, FFTSEG_OK otherwise.
+extern "C" int fftseg_noalloc_check(void)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "noalloc_check: cudaGetDevice");
+    if (dev < 0 || dev >= kNaMaxDevices) return set_error(FFTSEG_E_INVALID, "noalloc_check: device %d", dev);
+    float2 *base;
+    {
+        std::lock_guard<std::mutex> lock(g_na_mutex);
+        base = g_na_base[dev];
+    }
+    if (!base) return FFTSEG_OK;  // no call has run on this device
+    int *flag = reinterpret_cast<int *>(base + kNaOffCtr) + 1 + 2 * kNaMaxChunks;
+    int v = 0;
+    e = cudaMemcpy(&v, flag, sizeof(int), cudaMemcpyDeviceToHost);  // waits for the device
+    if (e != cudaSuccess) return cuda_error(e, "noalloc_check: read flag");
+    if (v) {
+        e = cudaMemset(flag, 0, sizeof(int));
+        if (e != cudaSuccess) return cuda_error(e, "noalloc_check: clear flag");
+        return set_error(FFTSEG_E_TIMEOUT,
+                         "exec_noalloc: a kernel gave up (flag %d): a bounded wait ran out or a shared buffer was "
+                         "misaligned; the outputs of the calls since the last check are not valid",
+                         v);
+    }
+    return FFTSEG_OK;
+}
