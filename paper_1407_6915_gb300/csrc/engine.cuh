@@ -130,6 +130,63 @@ HDEV void dft16(float2 *v)
     for (int k = 0; k < 16; ++k) v[k] = t[k];
 }
 
+// a * w_32^M, w_32 = exp(sigma 2 pi i / 32), M = 0..15, from cos(M pi/16)
+// and sin(M pi/16) (first-octant values c1 = cos(pi/16), s1 = sin(pi/16),
+// c3 = cos(3 pi/16), s3 = sin(3 pi/16), and those of rot16)
+template <int M, int S>
+HDEV float2 rot32(float2 a)
+{
+    static_assert(M >= 0 && M < 16, "rot32 exponent");
+    if constexpr (M == 0) return a;
+    else if constexpr (M == 8) return mul_si<S>(a);
+    else {
+        constexpr float c1 = 0.98078528040323044913f, s1 = 0.19509032201612826785f;
+        constexpr float c3 = 0.83146961230254523708f, s3 = 0.55557023301960222474f;
+        constexpr float CS[16][2] = {{1.f, 0.f},      {c1, s1},        {kC16a, kC16b},  {c3, s3},
+                                     {kC8, kC8},      {s3, c3},        {kC16b, kC16a},  {s1, c1},
+                                     {0.f, 1.f},      {-s1, c1},       {-kC16b, kC16a}, {-s3, c3},
+                                     {-kC8, kC8},     {-c3, s3},       {-kC16a, kC16b}, {-c1, s1}};
+        constexpr float C = CS[M][0], Sn = CS[M][1];
+        constexpr float s = (float)S;
+        return make_float2(a.x * C - s * a.y * Sn, a.y * C + s * a.x * Sn);
+    }
+}
+
+// 32 = 2 x 16: X_k = E_k + w_32^k O_k, X_{k+16} = E_k - w_32^k O_k, with E, O
+// the 16-point DFTs of the even and odd samples.
+template <int S>
+HDEV void dft32(float2 *v)
+{
+    float2 e[16], o[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        e[i] = v[2 * i];
+        o[i] = v[2 * i + 1];
+    }
+    dft16<S>(e);
+    dft16<S>(o);
+    o[1] = rot32<1, S>(o[1]);
+    o[2] = rot32<2, S>(o[2]);
+    o[3] = rot32<3, S>(o[3]);
+    o[4] = rot32<4, S>(o[4]);
+    o[5] = rot32<5, S>(o[5]);
+    o[6] = rot32<6, S>(o[6]);
+    o[7] = rot32<7, S>(o[7]);
+    o[8] = rot32<8, S>(o[8]);
+    o[9] = rot32<9, S>(o[9]);
+    o[10] = rot32<10, S>(o[10]);
+    o[11] = rot32<11, S>(o[11]);
+    o[12] = rot32<12, S>(o[12]);
+    o[13] = rot32<13, S>(o[13]);
+    o[14] = rot32<14, S>(o[14]);
+    o[15] = rot32<15, S>(o[15]);
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+        v[k] = cadd(e[k], o[k]);
+        v[k + 16] = csub(e[k], o[k]);
+    }
+}
+
 template <int R, int S>
 HDEV void dft(float2 *v)
 {
@@ -137,6 +194,7 @@ HDEV void dft(float2 *v)
     else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 8) dft8<S>(v);
     else if constexpr (R == 16) dft16<S>(v);
+    else if constexpr (R == 32) dft32<S>(v);
 }
 
 // Radix schedule of a length-2^LOG_L line: radix 16 while possible, then one

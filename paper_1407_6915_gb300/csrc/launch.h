@@ -38,6 +38,13 @@ cudaError_t launch_fourstep_ws(int log_n, int sign, const FourStepWsArgs &a, cud
 // output): producer warp, three swizzled TMA tile buffers, TMA output stores.
 struct FourStepHwArgs;
 cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t st);
+// Lane-line persistent four-step kernel for n = 2^16..2^20 (FP32, complex
+// output): lines of 256..1024 points with 32 points per lane, a queue of
+// column and row tiles, loader and retirer warps, swizzled TMA tiles.
+struct FourStepWlArgs;
+cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st);
+// Factorisation n = N1 x N2 and tile size E of the lane-line kernel.
+bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e);
 // Real-signal segments (k_real.cu): the pass between a length-n real DFT and
 // the length-m = n/2 complex DFT.  post: complex FFT output [nseg][m] -> the
 // n/2 + 1 bins [nseg][m + 1] (complex64, or float32 |X|^2 with power); pre:

@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <vector>
@@ -12,6 +13,7 @@
 #include "fourstep_ws.cuh"
 #include "launch.h"
 #include "fourstep_hw.cuh"
+#include "fourstep_wl.cuh"
 #include "plan.h"
 
 namespace fftseg {
@@ -28,12 +30,23 @@ constexpr int kRingNr = 3;
 
 bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 
-// The persistent four-step path runs on the warp-local-line kernel for
-// n = 256 x 256 with FP32 arithmetic and complex output.
+// FP32 complex output on the persistent four-step path, not asked for the
+// producer or CTA-tile kernels: the lane-local-line kernels can run it.
+bool lane_kernels_apply(const fftseg_plan_s *p)
+{
+    return p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
+           !(p->flags & (FFTSEG_FLAG_FOURSTEP_PRODUCER | FFTSEG_FLAG_FOURSTEP_TILES));
+}
+// n = 2^17..2^20 (and 2^16 on request): the lane-line kernel (fourstep_wl.cuh).
+bool uses_fourstep_wl(const fftseg_plan_s *p)
+{
+    return lane_kernels_apply(p) &&
+           ((p->log_n >= 17 && p->log_n <= 20) || (p->log_n == 16 && (p->flags & FFTSEG_FLAG_FOURSTEP_LANES)));
+}
+// n = 256 x 256 otherwise: the warp-line kernel (fourstep_hw.cuh).
 bool uses_fourstep_hw(const fftseg_plan_s *p)
 {
-    return p->log_n == 16 && p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
-           !(p->flags & FFTSEG_FLAG_FOURSTEP_PRODUCER);
+    return p->log_n == 16 && lane_kernels_apply(p) && !(p->flags & FFTSEG_FLAG_FOURSTEP_LANES);
 }
 // Bluestein plans whose M-point rows fit one block tile (M <= 4096, the
 // inner forward plan on the block path) run as one fused kernel.
@@ -162,10 +175,79 @@ void free_plan(fftseg_plan p)
     delete p;
 }
 
+int env_int(const char *name, int dflt, int lo, int hi)
+{
+    const char *v = getenv(name);
+    if (!v || !*v) return dflt;
+    const int x = atoi(v);
+    return x < lo ? lo : x > hi ? hi : x;
+}
+
+// Lane-line four-step kernel: its stage-2 tables, per-column-tile factors,
+// ring and per-segment counters.  Ring chunks of FFTSEG_WL_CHUNK_MB MiB
+// (default 16) and FFTSEG_WL_LOOKAHEAD chunks (default 1) of lead of the
+// column passes are tuning knobs read at plan creation.
+int build_fourstep_wl(fftseg_plan p)
+{
+    int l1, l2, le;
+    if (!fourstep_wl_shape(p->log_n, &l1, &l2, &le)) return set_error(FFTSEG_E_UNSUPPORTED, "lane-line shape");
+    p->path = PATH_FOURSTEP;
+    p->log_n1 = l1;
+    p->log_n2 = l2;
+    const int64_t n1 = int64_t(1) << l1, n2 = int64_t(1) << l2;
+    const int64_t p1 = n1 / 32, p2 = n2 / 32;
+    const int64_t wa = (int64_t(1) << le) / n1;  // columns per column tile
+    p->log_wa = le - l1;
+    p->log_wb = le - l2;
+    int rc;
+    // stage 2 of an L-point line: [r-1][b] = w_L^{b r}, r = 1 .. L/32 - 1, b < 32
+    auto stage2 = [&](float2 **dst, int64_t L) -> int {
+        const int64_t P = L / 32;
+        std::vector<float2> h((size_t)((P - 1) * 32));
+        for (int64_t r = 1; r < P; ++r) host_roots(h.data() + (r - 1) * 32, 32, L, r);
+        return upload(dst, h);
+    };
+    if ((rc = stage2(&p->twA, n1))) return rc;
+    if (l2 != l1 && (rc = stage2(&p->twB, n2))) return rc;
+    {
+        // per column tile ct: [wa cols][P1] w_n^{j2 j}, then [wa cols][32] scale * w_n^{j2 P1 m},
+        // j2 = ct wa + col
+        const int64_t ft = wa * (p1 + 32);
+        std::vector<float2> h((size_t)(n2 / wa * ft));
+        for (int64_t j2 = 0; j2 < n2; ++j2) {
+            float2 *t = h.data() + (j2 / wa) * ft;
+            const int64_t col = j2 % wa;
+            host_roots(t + col * p1, p1, p->n, j2);
+            float2 *f2 = t + wa * p1 + col * 32;
+            host_roots(f2, 32, p->n, j2 * p1);
+            for (int m = 0; m < 32; ++m) f2[m] = make_float2(f2[m].x * p->scale, f2[m].y * p->scale);
+        }
+        if ((rc = upload(&p->w4t, h))) return rc;
+    }
+    const int64_t chunk = (int64_t)env_int("FFTSEG_WL_CHUNK_MB", 16, 1, 64) << 20;
+    int64_t cs = chunk / (p->n * 8);
+    if (cs < 1) cs = 1;
+    if (cs > p->batch) cs = p->batch;
+    p->ring_cs = (int)cs;
+    p->wl_la = env_int("FFTSEG_WL_LOOKAHEAD", 1, 1, 4);
+    p->ring_nr = p->wl_la + 2;
+    cudaError_t e = cudaMalloc((void **)&p->ring, (size_t)(p->ring_nr * cs * p->n) * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(ring)");
+    const int64_t nc = (p->batch + cs - 1) / cs;
+    p->ctr_count = 1 + 2 * nc * cs;
+    e = cudaMalloc((void **)&p->ctr, (size_t)p->ctr_count * sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(counters)");
+    return FFTSEG_OK;
+}
+
 // Persistent four-step: ring, counters, stage tables and the two factor
 // tables of the four-step twiddle, [j2][k1 mod K] and [j2][k1 div K].
 int build_fourstep(fftseg_plan p)
 {
+    if ((p->flags & FFTSEG_FLAG_FOURSTEP_LANES) && !uses_fourstep_wl(p))
+        return set_error(FFTSEG_E_UNSUPPORTED,
+                         "plan_create: the lane-line four-step kernel runs FP32 complex output at n = 2^16..2^20");
+    if (uses_fourstep_wl(p)) return build_fourstep_wl(p);
     int l1, l2, lwa, lwb;
     if (!fourstep_shape(p->log_n, &l1, &l2, &lwa, &lwb))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: the four-step path needs n in [2^14, 2^24]");
@@ -244,7 +326,8 @@ int build_tc(fftseg_plan p)
 int build_fp32(fftseg_plan p)
 {
     const int ln = p->log_n;
-    if (p->flags & FFTSEG_FLAG_FOURSTEP_L2) return build_fourstep(p);
+    if (p->flags & (FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_LANES | FFTSEG_FLAG_FOURSTEP_TILES))
+        return build_fourstep(p);
     const bool force2 = (p->flags & FFTSEG_FLAG_FORCE_TWOPASS) && ln >= 8;
     int rc;
     if (ln <= 12 && !force2) {
@@ -333,6 +416,17 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
                    int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, bool swizzle128)
 {
+    return encode_tmap_3d_swz(m, base, d0, d1, d2, stride1_bytes, stride2_bytes, box0, box1, elem_bytes,
+                              swizzle128 ? 128 : 0);
+}
+
+int encode_tmap_3d_swz(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
+                       int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, int swizzle_bytes)
+{
+    const CUtensorMapSwizzle swz = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                   : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                   : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                         : CU_TENSOR_MAP_SWIZZLE_NONE;
     const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
     const cuuint64_t strides[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
     const cuuint32_t box[3] = {box0, box1, 1};
@@ -350,8 +444,7 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
     }
     CUresult r = encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
                         const_cast<void *>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
@@ -627,6 +720,41 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
                 e = launch_fourstep_ws(p->log_n, sign, a, st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
+                count_launches(1);
+                return FFTSEG_OK;
+            }
+            if (uses_fourstep_wl(p)) {
+                // lane-local lines of 256..1024 points, a queue of tiles, TMA loads and stores
+                FourStepWlArgs a{};
+                const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
+                const int64_t wa = int64_t(1) << p->log_wa, wb = int64_t(1) << p->log_wb;
+                const int64_t pwa = wa < 16 ? wa : 16, pwb = wb < 16 ? wb : 16;
+                const int64_t slabs = (int64_t)p->ring_nr * cs;
+                int rc = encode_tmap_3d_swz(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, (uint32_t)pwa, 256, 8,
+                                            (int)(pwa * 8));
+                if (rc == FFTSEG_OK)
+                    rc = encode_tmap_3d_swz(&a.tmB, p->ring, n1, n2, slabs, n1 * 8, n * 8, (uint32_t)pwb, 256, 8,
+                                            (int)(pwb * 8));
+                if (rc == FFTSEG_OK)
+                    rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8,
+                                            (int)(pwb * 8));
+                if (rc != FFTSEG_OK) return rc;
+                const int64_t nc = (nseg + cs - 1) / cs;
+                a.ring = p->ring;
+                a.twA = p->twA;
+                a.twB = p->twB ? p->twB : p->twA;
+                a.w4t = p->w4t;
+                a.ctr = p->ctr;
+                a.err = p->d_err;
+                a.nseg = nseg;
+                a.nchunks = (int)nc;
+                a.cs = cs;
+                a.nr = p->ring_nr;
+                a.la = p->wl_la;
+                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
+                if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+                e = launch_fourstep_wl(p->log_n, sign, a, st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
                 count_launches(1);
                 return FFTSEG_OK;

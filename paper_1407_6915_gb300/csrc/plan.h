@@ -50,7 +50,8 @@ struct fftseg_plan_s {
     int *ctr = nullptr;       // queue head + per-chunk counters
     int64_t ctr_count = 0;
     float2 *w4 = nullptr, *w4hi = nullptr;
-    float2 *w4t = nullptr;  // the warp-local-line kernel's factors, per column tile (see fourstep_hw.cuh)
+    float2 *w4t = nullptr;  // the warp-line and lane-line kernels' factors, per column tile
+    int wl_la = 0;          // lane-line kernel: chunks of lookahead of column over row passes
     int w4_log_k = 0;
     int log_wa = 0, log_wb = 0;
     // real-signal plans (FFTSEG_FLAG_REAL): a complex plan of n/2 points
@@ -88,10 +89,15 @@ void count_launches(int64_t k);
 // elem_bytes must be 128; the shared destination 1024-byte aligned).
 int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
                    int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes = 8, bool swizzle128 = false);
+// The same with the 32-, 64- or 128-byte swizzle (swizzle_bytes; 0: none):
+// box0 * elem_bytes must not exceed it, and the shared destination must be
+// aligned to the swizzle pattern's repeat (8 rows of the swizzle span).
+int encode_tmap_3d_swz(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
+                       int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, int swizzle_bytes);
 
 // Plan flags that select a schedule (the rest are options).
 constexpr unsigned kPathFlags = FFTSEG_FLAG_FORCE_TWOPASS | FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_PRODUCER |
-                                FFTSEG_FLAG_CLUSTER_LOG2(0xF);
+                                FFTSEG_FLAG_FOURSTEP_LANES | FFTSEG_FLAG_FOURSTEP_TILES | FFTSEG_FLAG_CLUSTER_LOG2(0xF);
 
 // Autotuner (tune.cu): the schedule flags of the fastest schedule for n on
 // the current GPU, timed on min(batch, 256 MiB of input) segments.

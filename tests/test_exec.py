@@ -70,10 +70,11 @@ def test_two_pass_forced_matches_oracle(log_n, direction):
 @pytest.mark.parametrize("log_n,B", [(14, 67), (15, 33), (16, 37), (17, 9), (18, 9), (19, 5), (20, 5), (21, 3),
                                      (22, 2)])
 @pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD)])
-@pytest.mark.parametrize("variant", [0, fs.FLAG_FOURSTEP_PRODUCER])
+@pytest.mark.parametrize("variant", [0, fs.FLAG_FOURSTEP_PRODUCER, fs.FLAG_FOURSTEP_TILES])
 def test_persistent_fourstep_matches_oracle(log_n, B, direction, norm, variant):
     # batches that span several chunks of the ring and end in a partial chunk;
-    # both the all-compute kernel and the producer/consumer kernel
+    # the default kernel for the length (lane-line at 2^17..2^20, warp-line at
+    # 2^16, CTA tiles elsewhere), the producer/consumer kernel and the CTA-tile kernel
     n = 1 << log_n
     x = siggen.tones(800 + log_n, B * n).reshape(B, n)
     plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2 | variant)
