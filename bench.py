@@ -35,15 +35,27 @@ UNIT = "GFLOP/s"
 WORKLOAD = "resident 8 GiB complex64 signal, 16384 segments x 65536 points, forward then inverse (1/n)"
 
 
-def workload_name(segments):
-    if segments == SEGMENTS:
+def workload_name(segments, n=N):
+    if segments == SEGMENTS and n == N:
         return WORKLOAD
     return ("resident %g GiB complex64 signal, %d segments x %d points, forward then inverse (1/n)"
-            % (segments * N * 8 / 2**30, segments, N))
+            % (segments * n * 8 / 2**30, segments, n))
 
 
-KERNELS = {"cluster": "k_cluster: one thread-block cluster per segment, all-to-all over distributed shared memory",
-           "four-step": "k_fourstep_hw: persistent four-step, warp-local lines, intermediate kept in L2"}
+def kernel_name(path, n, flags):
+    """The kernel a complex FP32 plan runs (for the roofline record)."""
+    import paper_1407_6915_gb300 as fs
+    if path == "cluster":
+        return "k_cluster: one thread-block cluster per segment, all-to-all over distributed shared memory"
+    if path != "four-step":
+        return path
+    if flags & (fs.FLAG_FOURSTEP_PRODUCER | fs.FLAG_FOURSTEP_TILES):
+        return "k_fourstep: persistent four-step over CTA tiles, intermediate kept in L2"
+    if n == 1 << 16 and flags & fs.FLAG_FOURSTEP_WARP_LINES:
+        return "k_fourstep_hw: persistent four-step, warp-local lines, intermediate kept in L2"
+    if (1 << 16) <= n <= (1 << 20):
+        return "k_fourstep_wl: persistent four-step, lane-local lines of 32 points per lane, intermediate kept in L2"
+    return "k_fourstep: persistent four-step over CTA tiles, intermediate kept in L2"
 
 
 def vendor_context(n, segments):
@@ -130,32 +142,83 @@ class Clocks:
 
 
 def cpu_baseline(seconds_target=12.0):
-    """The FP64 oracle as it stands, timed on this host's cores on a sample of the workload."""
+    """The FP64 oracle as it stands, timed on this host's cores on a sample of
+    the workload: with every core, and with one core on a smaller sample."""
     import numpy as np
     import oracle
     import siggen
     cores = os.cpu_count() or 1
+
+    def timed(seg, threads, target):
+        x = siggen.tones(SEED, seg * N).reshape(seg, N)
+        t0 = time.perf_counter()
+        X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=threads)
+        oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=threads)
+        dt = time.perf_counter() - t0
+        reps = min(64, max(1, int(target / max(dt, 1e-3))))
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=threads)
+            oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=threads)
+        dt = time.perf_counter() - t0
+        return 2 * flops_per_transform(N, seg * reps) / dt / 1e9, reps, dt
+
     seg = max(cores, 8)
-    x = siggen.tones(SEED, seg * N).reshape(seg, N)
-    t0 = time.perf_counter()
-    X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
-    oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
-    dt = time.perf_counter() - t0
-    reps = max(1, int(seconds_target / max(dt, 1e-3)))
-    reps = min(reps, 64)
-    t0 = time.perf_counter()
-    for _ in range(reps):
-        X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
-        oracle.fft(X.astype(np.complex64), oracle.INVERSE, oracle.NORM_BACKWARD, nthreads=cores)
-    dt = time.perf_counter() - t0
-    value = 2 * flops_per_transform(N, seg * reps) / dt / 1e9
+    value, reps, dt = timed(seg, cores, seconds_target)
+    v1, reps1, dt1 = timed(2, 1, seconds_target / 3)
     return {"value": round(value, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d of the 16384 segments, forward+inverse, %d repetitions, %.1f s wall"
-                      % (seg, reps, dt)}
+                      % (seg, reps, dt),
+            "single_core": {"value": round(v1, 3), "unit": UNIT, "cores": 1,
+                            "sample": "2 segments, forward+inverse, %d repetitions, %.1f s wall" % (reps1, dt1)}}
+
+
+def c1_bench(peak, pairs=16):
+    """C1, the paper's record size: 4096 segments x 1024 points (32 MiB)
+    forward, uniform input (seed 0), timed over `pairs` rotating input/output
+    buffer pairs (together larger than 4x L2), so every launch reads and
+    writes HBM.  Kernel time from CUDA events; the host time of the
+    fftseg_exec call (launch only, no synchronisation) beside it."""
+    import torch
+    import paper_1407_6915_gb300 as fs
+    import siggen
+    n, B = 1024, 4096
+    x0 = torch.from_numpy(siggen.uniform(0, B * n).reshape(B, n)).cuda()
+    ins = [x0.clone() for _ in range(pairs)]
+    outs = [torch.empty_like(x0) for _ in range(pairs)]
+    plan = fs.Plan(n, B, fs.FORWARD)
+    stream = torch.cuda.current_stream()
+    for i in range(pairs):
+        plan.exec_ptr(ins[i].data_ptr(), outs[i].data_ptr(), B, stream)
+    torch.cuda.synchronize()
+    plan.check()
+    reps = 8 * pairs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    host = 0.0
+    e0.record(stream)
+    for k in range(reps):
+        i = k % pairs
+        t0 = time.perf_counter()
+        plan.exec_ptr(ins[i].data_ptr(), outs[i].data_ptr(), B, stream)
+        host += time.perf_counter() - t0
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plan.check()
+    ms = e0.elapsed_time(e1) / reps
+    gbs = 16.0 * n * B / (ms / 1e3) / 1e9
+    ok = bool(torch.equal(outs[0], outs[pairs - 1]))  # same input, same bits
+    return {"workload": "4096 segments x 1024 points complex64, forward, uniform[-1,1) seed 0",
+            "path": plan.info()["path"], "ms": round(ms, 5),
+            "gflops": round(flops_per_transform(n, B) / (ms / 1e3) / 1e9, 1),
+            "gbs_algorithmic": round(gbs, 1), "hbm_frac": round(gbs / peak, 4),
+            "api_us_per_call": round(host / reps * 1e6, 2),
+            "l2": "%d rotating buffer pairs, %d MiB in all (L2 is about 126 MiB)" % (pairs, pairs * 64),
+            "outputs_equal_across_buffers": ok}
 
 
 # the translation unit that instantiates each path's kernel
-KERNEL_TU = {"four-step": "k_fourstep.cu", "cluster": "k_cluster.cu", "block": "k_lines.cu"}
+KERNEL_TU = {"four-step": ("k_fourstep.cu", "k_fourstep_wl.cu"), "cluster": ("k_cluster.cu",),
+             "block": ("k_lines.cu",)}
 
 
 def kernel_rev(path="four-step"):
@@ -166,7 +229,7 @@ def kernel_rev(path="four-step"):
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_1407_6915_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.endswith(".cuh") or name == KERNEL_TU.get(path):
+        if name.endswith(".cuh") or name in KERNEL_TU.get(path, ()):
             with open(os.path.join(csrc, name), "rb") as f:
                 h.update(name.encode() + f.read())
     return h.hexdigest()[:12]
@@ -222,41 +285,69 @@ def link_peaks(dev, gib=1, reps=3):
 
 
 def stream_bench(link, h_signal=None):
-    """The out-of-core stream on a bounded sample: the tones + noise signal
-    (seed 2) generated on the host as it is read, through fftseg_stream in
-    2^20-point segments with |X|^2 output, chunks of 64 segments; then a
-    host-resident batch of the same shape through fftseg_exec_host, which
-    leaves out the generator and shows the pipeline against the link."""
+    """C3, the out-of-core stream at its configured size: 128 GiB of complex64
+    signal in 2^20-point segments through fftseg_stream with |X|^2 output, in
+    chunks of 64 segments (512 MiB).
+
+    The tones + noise generator (seed 2) runs at about 1 GB/s on the box's
+    host cores, two orders of magnitude below the host link, so a stream fed
+    by it measures the generator.  The full-size run therefore reads a
+    host-resident source: 2 GiB of the seed-2 signal generated once into
+    pinned memory and read cyclically by the reader callback (several copy
+    threads), as a signal already in host memory would be.  The generator's
+    own rate and a generator-fed stream of 2 GiB are reported beside it; a
+    host-resident batch through fftseg_exec_host shows the same pipeline
+    without callbacks."""
     import ctypes
     import torch
     import paper_1407_6915_gb300 as fs
     import siggen
     n = 1 << 20
     chunk = 64
-    nseg = 1024  # 8 GiB of the 128 GiB signal
+    nseg = 16384  # 128 GiB
+    pool_segs = 256  # 2 GiB
     total = nseg * n * 8
-    flops = flops_per_transform(n, nseg)
+    cores = os.cpu_count() or 1
     plan = fs.Plan(n, chunk, fs.FORWARD, out_kind=fs.OUT_POWER)
-    src = siggen.source(siggen.KIND_TONES, 2, total)
+    pool = torch.empty(pool_segs * n, dtype=torch.complex64, pin_memory=True)
+    t0 = time.perf_counter()
+    siggen.fill_pointer(siggen.KIND_TONES, 2, 0, pool_segs * n, pool.data_ptr(), nthreads=cores)
+    gen_s = time.perf_counter() - t0
+    out = {"n": n, "segments": nseg, "chunk_segments": chunk, "input_bytes": total,
+           "generator": {"what": "tones + noise, seed 2, into pinned memory", "bytes": pool_segs * n * 8,
+                         "s": round(gen_s, 3), "gbs": round(pool_segs * n * 8 / gen_s / 1e9, 3), "threads": cores}}
+    # full size, host-resident source
+    src = siggen.pool_source(pool.data_ptr(), pool_segs * n * 8, total, nthreads=min(cores, 16))
     snk = siggen.sink(None)  # counts the bytes, keeps nothing
+    rc, committed = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(src), siggen.write_fn_ptr(),
+                                ctypes.addressof(snk), 1 << 32, 0, chunk)  # warm-up: 4 GiB
     t0 = time.perf_counter()
     rc, committed = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(src), siggen.write_fn_ptr(),
                                 ctypes.addressof(snk), total, 0, chunk)
     wall = time.perf_counter() - t0
     ph = plan.stream_phases()
     h2d_gbs, d2h_gbs = total / wall / 1e9, total / 2 / wall / 1e9
-    gen_gbs = total / (ph["read_ms"] / 1e3) / 1e9 if ph["read_ms"] > 0 else None
-    out = {"n": n, "segments": nseg, "chunk_segments": chunk, "input_bytes": total, "status": rc,
-           "output_bytes": int(snk.bytes_written), "wall_s": round(wall, 3),
-           "gflops": round(flops / wall / 1e9, 1),
-           "h2d_gbs": round(h2d_gbs, 2), "d2h_gbs": round(d2h_gbs, 2),
-           "link_frac": round(max(h2d_gbs / link["h2d"], d2h_gbs / link["d2h"]), 4),
-           "phases_ms": {k: round(v, 1) for k, v in ph.items()},
-           "generator_gbs": round(gen_gbs, 2) if gen_gbs else None,
-           "generator_threads": int(src.nthreads),
-           "bound": "generator" if ph["read_ms"] > 0.8 * ph["wall_ms"] else "pipeline",
-           "full_128gib_s_extrapolated": round(wall * 16, 1)}
+    out.update({"source": "2 GiB pinned pool of the seed-2 signal, read cyclically (%d copy threads)" % src.nthreads,
+                "status": rc, "committed_bytes": int(committed), "wall_s": round(wall, 3),
+                "gflops": round(flops_per_transform(n, nseg) / wall / 1e9, 1),
+                "h2d_gbs": round(h2d_gbs, 2), "d2h_gbs": round(d2h_gbs, 2),
+                "link_frac": round(max(h2d_gbs / link["h2d"], d2h_gbs / link["d2h"]), 4),
+                "phases_ms": {k: round(v, 1) for k, v in ph.items()},
+                "bound": "reader" if ph["read_ms"] > 0.8 * ph["wall_ms"] else "pipeline"})
+    # a generator-fed sample (2 GiB)
+    gseg = 256
+    gsrc = siggen.source(siggen.KIND_TONES, 2, gseg * n * 8)
+    t0 = time.perf_counter()
+    grc, _ = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(gsrc), siggen.write_fn_ptr(),
+                         ctypes.addressof(snk), gseg * n * 8, 0, chunk)
+    gwall = time.perf_counter() - t0
+    gph = plan.stream_phases()
+    out["generator_fed_sample"] = {"segments": gseg, "status": grc, "wall_s": round(gwall, 3),
+                                   "h2d_gbs": round(gseg * n * 8 / gwall / 1e9, 2),
+                                   "bound": "generator" if gph["read_ms"] > 0.8 * gph["wall_ms"] else "pipeline",
+                                   "full_128gib_s_at_this_rate": round(gwall * nseg / gseg, 1)}
     plan.destroy()
+    del pool
     if h_signal is not None:
         hn = min(h_signal.numel() // n, 512)
         hp = fs.Plan(n, chunk, fs.FORWARD, out_kind=fs.OUT_POWER)
@@ -550,17 +641,34 @@ def bluestein_bench(peak):
 def tune_table():
     """The autotuner's choice per length (FP32, complex output, a 256 MiB batch)
     beside the library's default schedule."""
+    import torch
     import paper_1407_6915_gb300 as fs
     rows = []
+    x = torch.zeros(1 << 25, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
     for log_n in range(13, 25):
         n = 1 << log_n
-        flags, ms = fs.autotune(n, max(1, (1 << 25) // n))
-        plan = fs.Plan(n, 1, fs.FORWARD)
+        B = max(1, (1 << 25) // n)
+        flags, ms = fs.autotune(n, B)
+        plan = fs.Plan(n, B, fs.FORWARD)
         default = plan.info()["path"]
+        # the default schedule, timed the way the tuner times its candidates
+        for _ in range(3):
+            plan.exec(x.view(B, n), out=y.view(B, n))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            plan.exec(x.view(B, n), out=y.view(B, n))
+        e1.record()
+        torch.cuda.synchronize()
+        plan.check()
+        dms = e0.elapsed_time(e1) / 10
         plan.destroy()
         plan = fs.Plan(n, 1, fs.FORWARD, flags=flags)
         rows.append({"n": n, "tuned_flags": hex(flags), "tuned_path": plan.info()["path"],
-                     "tuned_ms_per_256mib": round(ms, 4), "default_path": default})
+                     "tuned_ms_per_256mib": round(ms, 4), "default_path": default,
+                     "default_ms_per_256mib": round(dms, 4),
+                     "default_over_tuned": round(dms / ms, 3) if ms > 0 else None})
         plan.destroy()
     return rows
 
@@ -592,7 +700,7 @@ def serve_bench(peak, njobs=600, seed=5):
     ring = torch.empty(ring_elems, dtype=torch.complex64, device="cuda")
     budget = 32 << 30
 
-    def run(arrivals):
+    def run(arrivals, subset=None):
         srv = fs.Server(hbm_budget_bytes=budget, max_inflight_jobs=256)
         lat = [None] * len(jobs)
         pos = 0
@@ -600,6 +708,8 @@ def serve_bench(peak, njobs=600, seed=5):
         with cf.ThreadPoolExecutor(max_workers=512) as ex:
             futs = []
             for i, (n, nseg, direction, norm) in enumerate(jobs):
+                if subset is not None and i not in subset:
+                    continue
                 if arrivals is not None:
                     wait = t0 + arrivals[i] - time.perf_counter()
                     if wait > 0:
@@ -642,9 +752,22 @@ def serve_bench(peak, njobs=600, seed=5):
                       "hbm_frac": round(16.0 * samples / wall / 1e9 / peak, 4),
                       "jobs_ok": len(ok), "launches": stats["launches"],
                       "peak_admitted_bytes": stats["peak_admitted_bytes"]})
+    # where the saturated time goes: each length class's jobs run alone (queued at once)
+    classes = (("n <= 4096 (ragged kernel)", 1 << 8, 1 << 12), ("2^13..2^16", 1 << 13, 1 << 16),
+               ("2^17..2^20", 1 << 17, 1 << 20), ("2^21..2^22", 1 << 21, 1 << 22))
+    per_class = []
+    for name, lo, hi in classes:
+        sub = {i for i, (n, _, _, _) in enumerate(jobs) if lo <= n <= hi}
+        if not sub:
+            continue
+        cs = sum(jobs[i][0] * jobs[i][1] for i in sub)
+        _, wall_c, _ = run(None, sub)
+        per_class.append({"class": name, "jobs": len(sub), "sample_share": round(cs / samples, 4),
+                          "alone_s": round(wall_c, 4), "share_of_saturated_time": round(wall_c / wall_sat, 4),
+                          "hbm_frac_alone": round(16.0 * cs / wall_c / 1e9 / peak, 4)})
     del ring, x
     torch.cuda.empty_cache()
-    return {"jobs": njobs, "budget_bytes": budget,
+    return {"jobs": njobs, "budget_bytes": budget, "per_length_class": per_class,
             "job_recipe": "n = 2^e, e uniform in 8..22; segments 2^U(0,12) capped at 2^28 samples per job; "
                           "50/50 forward / inverse(1/n); uniform[-1,1) input",
             "saturated_gflops": round(flops / wall_sat / 1e9, 1),
@@ -678,7 +801,7 @@ def run_reference(args):
     import oracle
     import siggen
     cores = os.cpu_count() or 1
-    seg = max(cores // 2, 4)  # a bounded sample per step: a few seconds of CPU work
+    seg = 2 * cores  # a bounded sample per step on every core: a few seconds of CPU work
     x = siggen.tones(SEED, seg * N).reshape(seg, N)
     for _ in range(args.warmup):
         X = oracle.fft(x, oracle.FORWARD, oracle.NORM_NONE, nthreads=cores)
@@ -716,17 +839,19 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream()
-    S = args.segments
+    n = args.n
+    S = args.segments if args.segments else (SEGMENTS if n == n else max(1, (1 << 30) // n))
+    pflags = args.flags
 
     # ---- inputs: synthesised on the host straight into pinned memory
-    h_in = torch.empty(S * N, dtype=torch.complex64, pin_memory=True)
-    siggen.fill_pointer(siggen.KIND_TONES, SEED, 0, S * N, h_in.data_ptr())
-    h_out = torch.empty(S * N, dtype=torch.complex64, pin_memory=True)
-    x = h_in.to(dev).view(S, N)
+    h_in = torch.empty(S * n, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_TONES, SEED, 0, S * n, h_in.data_ptr())
+    h_out = torch.empty(S * n, dtype=torch.complex64, pin_memory=True)
+    x = h_in.to(dev).view(S, n)
     y = torch.empty_like(x)
     z = torch.empty_like(x)
-    fwd = fs.Plan(N, S, fs.FORWARD, fs.NORM_NONE)
-    inv = fs.Plan(N, S, fs.INVERSE, fs.NORM_BACKWARD)
+    fwd = fs.Plan(n, S, fs.FORWARD, fs.NORM_NONE, flags=pflags)
+    inv = fs.Plan(n, S, fs.INVERSE, fs.NORM_BACKWARD, flags=pflags)
 
     def step():
         fwd.exec_ptr(x.data_ptr(), y.data_ptr(), S, stream)
@@ -767,7 +892,7 @@ def run_ours(args):
     kernel_ms = [a.elapsed_time(b) for a, b, _ in evs] + [b.elapsed_time(c) for _, b, c in evs]
     ms = max_over_ranks(ms, dev)
     ms_per_step = ms / args.steps
-    flops_step = 2 * flops_per_transform(N, S)
+    flops_step = 2 * flops_per_transform(n, S)
     value = world * flops_step / (ms_per_step / 1e3) / 1e9
 
     # round-trip check of this very run (inverse(forward(x)) == x up to rounding)
@@ -776,67 +901,72 @@ def run_ours(args):
     # ---- roofline of the dominant kernel: algorithmic bytes per launch / mean launch time
     peak, peak_kind = peaks()
     per_launch_ms = statistics.mean(kernel_ms)
-    algo_bytes = 16.0 * N * S
+    algo_bytes = 16.0 * n * S
     achieved = algo_bytes / (per_launch_ms / 1e3) / 1e9
-    traffic = measured_traffic("%s:%d" % (fwd.info()["path"], N))
+    traffic = measured_traffic("%s:%d" % (fwd.info()["path"], n))
 
     # ---- end to end through the public API with host buffers: fftseg_exec_host
     # runs the forward + inverse chain over the pinned host signal in chunks,
     # copies in both directions overlapped with the transforms
     # (untimed warm-up calls: the first host transfers after an idle spell run
     # several times slower while the host link ramps up)
-    e2e_steps = min(max(args.steps, 10), 20)  # isolated slow host transfers weigh less over more steps
-    e2e_warm = max(args.warmup, 6)  # the first host transfers after an idle spell ramp up slowly
-    for _ in range(e2e_warm):
-        fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)
-    barrier()
-    t0 = time.perf_counter()
-    e2e_step_ms = []
-    for _ in range(e2e_steps):
-        t1 = time.perf_counter()
-        fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)  # synchronous
-        e2e_step_ms.append(round((time.perf_counter() - t1) * 1e3, 2))
-    torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_value = world * flops_step / e2e_s / 1e9
-    link = link_peaks(dev)
-    k = min(S, 4)
-    e2e_err = float(torch.linalg.vector_norm((h_out[: k * N] - h_in[: k * N])) / torch.linalg.vector_norm(h_in[: k * N]))
+    e2e, link = None, None
+    if not args.no_e2e:
+        e2e_steps = min(max(args.steps, 10), 20)  # isolated slow host transfers weigh less over more steps
+        e2e_warm = max(args.warmup, 6)  # the first host transfers after an idle spell ramp up slowly
+        for _ in range(e2e_warm):
+            fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)
+        barrier()
+        t0 = time.perf_counter()
+        e2e_step_ms = []
+        for _ in range(e2e_steps):
+            t1 = time.perf_counter()
+            fs.exec_host([fwd, inv], h_in.data_ptr(), h_out.data_ptr(), S)  # synchronous
+            e2e_step_ms.append(round((time.perf_counter() - t1) * 1e3, 2))
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_value = world * flops_step / e2e_s / 1e9
+        link = link_peaks(dev)
+        k = min(S, 4)
+        e2e_err = float(torch.linalg.vector_norm((h_out[: k * n] - h_in[: k * n])) / torch.linalg.vector_norm(h_in[: k * n]))
+        e2e = {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
+               "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2),
+               "step_ms": e2e_step_ms, "median_step_ms": round(statistics.median(e2e_step_ms), 2),
+               "warmup_calls": e2e_warm, "call": "fftseg_exec_host([forward, inverse]) on pinned host buffers",
+               "link_gbs_each_way": round(x.numel() * 8 / e2e_s / 1e9, 1),
+               "link_peaks_gbs": link,
+               "link_frac": round(x.numel() * 8 / e2e_s / 1e9 / link["concurrent_each_way"], 4),
+               "round_trip_rel_l2_first_%d_segments" % k: e2e_err}
 
     line = None
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": workload_name(S), "n": N, "segments": S, "path": fwd.info()["path"],
+                "config": {"workload": workload_name(S, n), "n": n, "segments": S, "path": fwd.info()["path"],
                            "signal": "32 off-bin tones (log-uniform 1e-3..1) + complex Gaussian noise sigma 0.1, seed 1",
-                           "l2": "inputs larger than L2 (%g GiB per buffer), no flush needed" % (S * N * 8 / 2**30),
+                           "l2": "inputs larger than L2 (%g GiB per buffer), no flush needed" % (S * n * 8 / 2**30),
                            "replicas": "one independent replica per GPU (no collective on the data path)"},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "traffic": traffic,
                              "peak_kind": peak_kind,
-                             "kernel": KERNELS.get(fwd.info()["path"], fwd.info()["path"]) +
+                             "kernel": kernel_name(fwd.info()["path"], n, pflags) +
                              " (one launch per transform, one HBM pass)",
                              "algorithmic_bytes_per_launch": algo_bytes,
                              "mean_launch_ms": round(per_launch_ms, 4)},
-                "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * 8),
-                        "d2h_bytes_per_step": int(z.numel() * 8), "ms_per_step": round(e2e_s * 1e3, 2),
-                        "step_ms": e2e_step_ms, "median_step_ms": round(statistics.median(e2e_step_ms), 2),
-                        "warmup_calls": e2e_warm, "call": "fftseg_exec_host([forward, inverse]) on pinned host buffers",
-                        "link_gbs_each_way": round(x.numel() * 8 / e2e_s / 1e9, 1),
-                        "link_peaks_gbs": link,
-                        "link_frac": round(x.numel() * 8 / e2e_s / 1e9 / link["concurrent_each_way"], 4),
-                        "round_trip_rel_l2_first_%d_segments" % k: e2e_err},
                 "gpu_launches": int(launches),
                 "clocks": clk.summary(),
                 "round_trip_rel_l2": err}
+        if e2e is not None:
+            line["e2e"] = e2e
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline()
         if world == 1 and not args.no_extras:
             del x, y, z
             torch.cuda.empty_cache()
-            line["vendor_fft_context"] = extra(vendor_context, N, S)
-            line["stream"] = extra(stream_bench, link, h_in)
+            line["vendor_fft_context"] = extra(vendor_context, n, S)
+            line["c1"] = extra(c1_bench, peak)
+            line["stream"] = extra(stream_bench, link or link_peaks(dev), h_in)
             line["tc_split"] = extra(tc_split, peak)
             line["real"] = extra(real_bench, peak)
             line["frames"] = extra(frames_bench, peak)
@@ -861,8 +991,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the tensor-core split and the serving run")
-    ap.add_argument("--segments", type=int, default=SEGMENTS,
-                    help="segments per transform (default 16384; smaller only for profiler captures)")
+    ap.add_argument("--segments", type=int, default=0,
+                    help="segments per transform (default 16384 at n = 65536, else 2^30 / n; "
+                         "smaller only for profiler captures)")
+    ap.add_argument("--n", type=int, default=N,
+                    help="points per segment (default 65536, the benchmarked workload; other lengths only for "
+                         "profiler captures of their kernels)")
+    ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="plan flags (profiler captures)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -87,15 +87,22 @@ enum { FFTSEG_WINDOW_RECT = 0, FFTSEG_WINDOW_HANN = 1 };
    complex values, plus one pass that splits (forward) or joins (inverse) the
    spectra of the even and odd samples, in chunks whose intermediate stays in L2. */
 #define FFTSEG_FLAG_REAL 0x20u
-/* four-step path, FP32, complex output: the kernel with lane-local lines of
-   256..1024 points (32 points per lane, loader and retirer warps, a queue of
-   tiles).  It is the default for n = 2^17..2^20; this flag asks for it at
-   n = 2^16 too (whose default is the 256 x 256 warp-line kernel). */
-#define FFTSEG_FLAG_FOURSTEP_LANES 0x40u
+/* four-step path, FP32, complex output, n = 2^16: the 256 x 256 warp-line
+   kernel (16 points per lane, three CTAs per SM) instead of the default
+   lane-line kernel (32 points per lane, lines of 256..1024 points, the
+   default for n = 2^16..2^20) */
+#define FFTSEG_FLAG_FOURSTEP_WARP_LINES 0x40u
 /* four-step path on the CTA-tile kernel (tiles of whole CTAs, the form that
    also runs |X|^2 output and the tensor-core stages), instead of the
    lane-line kernels */
 #define FFTSEG_FLAG_FOURSTEP_TILES 0x80u
+/* test only, for the lane-line kernel: the row tiles of the first segment wait
+   for a counter value that is never reached, with a short spin limit, so that
+   the bounded wait runs out: the kernel records it in the plan's flag and
+   completes (that segment's output is not valid), and fftseg_plan_check then
+   returns FFTSEG_E_TIMEOUT.  Shows that a lost dependency ends in an error
+   status, not a hang. */
+#define FFTSEG_FLAG_TEST_STALL 0x1000u
 
 #define FFTSEG_MAX_LOG2N 24
 

@@ -24,7 +24,8 @@ OUT_COMPLEX, OUT_POWER = 0, 1
 FLAG_ZERO_PAD, FLAG_FORCE_TWOPASS, FLAG_FOURSTEP_L2, FLAG_FOURSTEP_PRODUCER = 0x1, 0x2, 0x4, 0x8
 FLAG_AUTOTUNE = 0x10
 FLAG_REAL = 0x20
-FLAG_FOURSTEP_LANES, FLAG_FOURSTEP_TILES = 0x40, 0x80
+FLAG_FOURSTEP_WARP_LINES, FLAG_FOURSTEP_TILES = 0x40, 0x80
+FLAG_TEST_STALL = 0x1000
 FILE_DIRECT, FILE_KEEP = 0x1, 0x2
 
 

@@ -393,6 +393,17 @@ FDEV void tma_load_3d(void *dst, const CUtensorMap *tmap, int x, int y, int z, u
         : "memory");
 }
 
+// Tiled 4-D TMA load of one box of `tmap` at element coordinates (x, y, z, w)
+// into shared memory, completed on *bar (x * element size a multiple of 16).
+FDEV void tma_load_4d(void *dst, const CUtensorMap *tmap, int x, int y, int z, int w, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // L2 cache policy: lines fetched or written under it are evicted first (for
 // data streamed once, so that it does not displace data kept in L2).
 FDEV uint64_t policy_evict_first()

@@ -80,10 +80,11 @@ struct FourStepShape {
     static_assert(StageInfo<LOG_N1, 0>::NSTAGES >= 2 && StageInfo<LOG_N2, 0>::NSTAGES >= 2, "two stages per pass");
 };
 
-// bounded spin until *p >= target (acquire); false if it never got there
-FDEV bool spin_until(const int *p, int target, int *err)
+// bounded spin until *p >= target (acquire); false (and bit 4 of *err set)
+// if it never got there within `limit` polls
+FDEV bool spin_until(const int *p, int target, int *err, uint32_t limit = 1u << 22)
 {
-    for (uint32_t it = 0; it < (1u << 22); ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         int v;
         asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
         if (v >= target) return true;

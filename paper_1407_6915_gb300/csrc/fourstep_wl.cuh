@@ -4,7 +4,10 @@
 // The factorisation is the one of k_fourstep and k_fourstep_hw:
 //   pass A (column DFTs): Yt[j2][k1] = w_n^{j2 k1} sum_{j1} x[j1 N2 + j2] w_{N1}^{j1 k1}
 //   pass B (row DFTs):    X[k1 + N1 k2] = sum_{j2} Yt[j2][k1] w_{N2}^{j2 k2}
-// with Yt in an L2-resident ring of chunk buffers; a row tile of segment s
+// with Yt in an L2-resident ring of chunk buffers, stored in blocks of the
+// row tiles' W_B rows, [k1 / W_B][j2][k1 mod W_B], so that every row tile is
+// one contiguous block (its TMA load is one region, and once it is consumed
+// its L2 lines are dropped whole); a row tile of segment s
 // waits for the column tiles of s, a column tile for the row tiles of the
 // segment that last used its ring slot (per-segment counters).
 //
@@ -48,12 +51,13 @@ namespace fftseg {
 
 struct FourStepWlArgs {
     CUtensorMap tmA;     // input  [nseg][N1][N2], box [PW_A][256][1], swizzled
-    CUtensorMap tmB;     // ring   [slabs][N2][N1], box [PW_B][256][1], swizzled
+    CUtensorMap tmB;     // ring   [slabs][N1/W_B][N2][W_B], box [PW_B][256][1][1], swizzled
     CUtensorMap tmO;     // output [nseg][N2][N1], box [PW_B][256][1], swizzled
-    float2 *ring;        // nr*cs segments, [slot*cs + sl][j2][k1]
+    float2 *ring;        // nr*cs segments, [slot*cs + sl][k1 / W_B][j2][k1 mod W_B]
     const float2 *twA;   // stage-2 twiddles of an N1-point line: [r-1][b] = w_{N1}^{b r}, r < P1, b < 32
     const float2 *twB;   // the same for N2
-    const float2 *w4t;   // per column tile ct: [W_A cols][P1] w_n^{j2 j}, then [W_A cols][32] scale * w_n^{j2 P1 m}
+    const float2 *w4t;   // per column tile ct, columns in pairs (c / 2, c mod 2 fastest):
+                         // [W_A/2][P1][2] w_n^{j2 j}, then [W_A/2][32][2] scale * w_n^{j2 P1 m}
     int *ctr;            // [0] queue head, [1 + s] column tiles of s done, [1 + nc*cs + s] row tiles of s done
     int *err;
     int64_t nseg;
@@ -61,6 +65,8 @@ struct FourStepWlArgs {
     int cs;              // segments per chunk
     int nr;              // ring chunks (>= la + 2)
     int la;              // column passes run this many chunks ahead of row passes (>= 1)
+    int stall;           // test only: segment 0's row tiles wait for one column tile more than
+                         // exists, with a short spin limit, so that the bounded wait runs out
 };
 
 // One pass over lines of L = 2^LOG_L points in tiles of E = 2^LOG_E points.
@@ -251,15 +257,12 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                     }
                     mbar_arrive(&empty[b]);
                 }
-                if constexpr (PB::W * 8 % 128 == 0) {
-                    if (valid) {
-                    // the tile's ring lines (whole 128-byte lines) were consumed: drop them
-                    constexpr int LPR = PB::W * 8 / 128;  // lines per ring row
-                    const float2 *tile = a.ring + (int64_t)slab * N + rt * PB::W;
-                    for (int l = lane; l < Sh::N2 * LPR; l += 32)
-                        discard_l2_line(tile + (int64_t)(l / LPR) * N1 + (l % LPR) * 16);
+                if (valid) {
+                    // the tile's ring block was consumed: drop its lines from L2
+                    constexpr int LINES = Sh::N2 * PB::W * 8 / 128;
+                    const float2 *tile = a.ring + (int64_t)slab * N + (int64_t)rt * Sh::N2 * PB::W;
+                    for (int l = lane; l < LINES; l += 32) discard_l2_line(tile + (int64_t)l * 16);
                     __syncwarp();
-                    }
                 }
                 pend[npend++] = doneB + s;
             }
@@ -327,7 +330,9 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                 // the dependency first (its probe's latency overlaps the wait for a buffer)
                 if (s < a.nseg) {
                     if (isb && s > a_seen) {
-                        if (spin_until(doneA + s, Sh::TSEG_A, a.err)) a_seen = s;
+                        const bool stall = a.stall && s == 0;
+                        if (spin_until(doneA + s, Sh::TSEG_A + (stall ? 1 : 0), a.err, stall ? 4096u : 1u << 22))
+                            a_seen = s;
                     } else if (!isb && s >= ring_segs && s - ring_segs > b_seen) {
                         if (spin_until(doneB + (s - ring_segs), Sh::TSEG_B, a.err)) b_seen = s - ring_segs;
                     }
@@ -365,8 +370,8 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                             for (int p = 0; p < PB::NPANEL; ++p)
 #pragma unroll
                                 for (int q = 0; q < PB::NBOXY; ++q)
-                                    tma_load_3d(dst + p * PB::PANEL_BYTES + q * 256 * PB::ROWB, &a.tmB,
-                                                tile * PB::W + p * PB::PW, q * 256, slab, &full[b]);
+                                    tma_load_4d(dst + p * PB::PANEL_BYTES + q * 256 * PB::ROWB, &a.tmB,
+                                                p * PB::PW, q * 256, tile, slab, &full[b]);
                         }
                     } else {
                         // an absent segment of the last chunk: nothing to load, but its
@@ -407,16 +412,26 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             wl_line<PS, S>(v, Pc, tb, c, j, group, TWA);
             // times w_n^{j2 k1}, k1 = j + P m: w_n^{j2 j} w_n^{j2 P m} (scale folded in), into the ring
             const float2 *Fb = F + bb * PS::FT;
-            const float2 f1 = Fb[c * PS::P + j];
-            float2 *dst = a.ring + (int64_t)slab * N + (int64_t)(ct * PS::W + c) * N1 + j;
+            const float2 f1 = Fb[((c >> 1) * PS::P + j) * 2 + (c & 1)];
+            const float2 *f2p = Fb + PS::W * PS::P + (c >> 1) * 64 + (c & 1);
+            // ring block layout [k1 / W_B][j2][k1 mod W_B], k1 = j + P m
+            constexpr int WB = PB::W;
+            constexpr int64_t BLK = (int64_t)Sh::N2 * WB;
+            const int j2 = ct * PS::W + c;
+            float2 *row = a.ring + (int64_t)slab * N + (int64_t)j2 * WB;
+            float2 *dst = PS::P >= WB ? row + (int64_t)(j / WB) * BLK + (j % WB) : row + j;
 #pragma unroll
             for (int e = 0; e < PS::Q; ++e)
 #pragma unroll
                 for (int r = 0; r < PS::P; ++r) {
                     const int mm = e + PS::Q * r;
-                    const float2 f2 = Fb[PS::W * PS::P + c * 32 + mm];
+                    const float2 f2 = f2p[2 * mm];
                     const float2 wv = make_float2(f1.x * f2.x - f1.y * f2.y, f1.x * f2.y + f1.y * f2.x);
-                    dst[PS::P * mm] = twmul<S>(v[e * PS::P + r], wv);
+                    // P >= W_B: k1 / W_B = j / W_B + m P / W_B, k1 mod W_B = j mod W_B;
+                    // else (W_B a multiple of P, j < P): k1 / W_B = m P / W_B, k1 mod W_B = j + m P mod W_B
+                    const int64_t off = PS::P >= WB ? (int64_t)mm * (PS::P / WB) * BLK
+                                                    : (int64_t)(mm * PS::P / WB) * BLK + (mm * PS::P) % WB;
+                    dst[off] = twmul<S>(v[e * PS::P + r], wv);
                 }
             (void)s;
         } else if (kind == KIND_B) {

@@ -37,16 +37,17 @@ bool lane_kernels_apply(const fftseg_plan_s *p)
     return p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
            !(p->flags & (FFTSEG_FLAG_FOURSTEP_PRODUCER | FFTSEG_FLAG_FOURSTEP_TILES));
 }
-// n = 2^17..2^20 (and 2^16 on request): the lane-line kernel (fourstep_wl.cuh).
+// n = 2^16..2^20: the lane-line kernel (fourstep_wl.cuh), measured faster
+// than the warp-line kernel at 2^16 (0.60 against 0.59 of the copy peak).
 bool uses_fourstep_wl(const fftseg_plan_s *p)
 {
-    return lane_kernels_apply(p) &&
-           ((p->log_n >= 17 && p->log_n <= 20) || (p->log_n == 16 && (p->flags & FFTSEG_FLAG_FOURSTEP_LANES)));
+    return lane_kernels_apply(p) && p->log_n >= 16 && p->log_n <= 20 &&
+           !(p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
 }
-// n = 256 x 256 otherwise: the warp-line kernel (fourstep_hw.cuh).
+// n = 256 x 256 on request: the warp-line kernel (fourstep_hw.cuh).
 bool uses_fourstep_hw(const fftseg_plan_s *p)
 {
-    return p->log_n == 16 && lane_kernels_apply(p) && !(p->flags & FFTSEG_FLAG_FOURSTEP_LANES);
+    return p->log_n == 16 && lane_kernels_apply(p) && (p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
 }
 // Bluestein plans whose M-point rows fit one block tile (M <= 4096, the
 // inner forward plan on the block path) run as one fused kernel.
@@ -185,7 +186,7 @@ int env_int(const char *name, int dflt, int lo, int hi)
 
 // Lane-line four-step kernel: its stage-2 tables, per-column-tile factors,
 // ring and per-segment counters.  Ring chunks of FFTSEG_WL_CHUNK_MB MiB
-// (default 16) and FFTSEG_WL_LOOKAHEAD chunks (default 1) of lead of the
+// (default 24) and FFTSEG_WL_LOOKAHEAD chunks (default 1) of lead of the
 // column passes are tuning knobs read at plan creation.
 int build_fourstep_wl(fftseg_plan p)
 {
@@ -210,21 +211,25 @@ int build_fourstep_wl(fftseg_plan p)
     if ((rc = stage2(&p->twA, n1))) return rc;
     if (l2 != l1 && (rc = stage2(&p->twB, n2))) return rc;
     {
-        // per column tile ct: [wa cols][P1] w_n^{j2 j}, then [wa cols][32] scale * w_n^{j2 P1 m},
-        // j2 = ct wa + col
+        // per column tile ct, its columns col (j2 = ct wa + col) in pairs, the
+        // pair's two columns side by side (so that the two lines a half-warp
+        // holds read adjacent entries): [wa/2][P1][2] w_n^{j2 j}, then
+        // [wa/2][32][2] scale * w_n^{j2 P1 m}
         const int64_t ft = wa * (p1 + 32);
         std::vector<float2> h((size_t)(n2 / wa * ft));
+        std::vector<float2> t1((size_t)p1), t2(32);
         for (int64_t j2 = 0; j2 < n2; ++j2) {
             float2 *t = h.data() + (j2 / wa) * ft;
-            const int64_t col = j2 % wa;
-            host_roots(t + col * p1, p1, p->n, j2);
-            float2 *f2 = t + wa * p1 + col * 32;
-            host_roots(f2, 32, p->n, j2 * p1);
-            for (int m = 0; m < 32; ++m) f2[m] = make_float2(f2[m].x * p->scale, f2[m].y * p->scale);
+            const int64_t col = j2 % wa, pr = col >> 1, hc = col & 1;
+            host_roots(t1.data(), p1, p->n, j2);
+            host_roots(t2.data(), 32, p->n, j2 * p1);
+            for (int64_t j = 0; j < p1; ++j) t[(pr * p1 + j) * 2 + hc] = t1[(size_t)j];
+            for (int m = 0; m < 32; ++m)
+                t[wa * p1 + (pr * 32 + m) * 2 + hc] = make_float2(t2[m].x * p->scale, t2[m].y * p->scale);
         }
         if ((rc = upload(&p->w4t, h))) return rc;
     }
-    const int64_t chunk = (int64_t)env_int("FFTSEG_WL_CHUNK_MB", 16, 1, 64) << 20;
+    const int64_t chunk = (int64_t)env_int("FFTSEG_WL_CHUNK_MB", 24, 1, 64) << 20;
     int64_t cs = chunk / (p->n * 8);
     if (cs < 1) cs = 1;
     if (cs > p->batch) cs = p->batch;
@@ -244,9 +249,9 @@ int build_fourstep_wl(fftseg_plan p)
 // tables of the four-step twiddle, [j2][k1 mod K] and [j2][k1 div K].
 int build_fourstep(fftseg_plan p)
 {
-    if ((p->flags & FFTSEG_FLAG_FOURSTEP_LANES) && !uses_fourstep_wl(p))
+    if ((p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES) && !uses_fourstep_hw(p))
         return set_error(FFTSEG_E_UNSUPPORTED,
-                         "plan_create: the lane-line four-step kernel runs FP32 complex output at n = 2^16..2^20");
+                         "plan_create: the warp-line four-step kernel runs FP32 complex output at n = 2^16");
     if (uses_fourstep_wl(p)) return build_fourstep_wl(p);
     int l1, l2, lwa, lwb;
     if (!fourstep_shape(p->log_n, &l1, &l2, &lwa, &lwb))
@@ -326,7 +331,7 @@ int build_tc(fftseg_plan p)
 int build_fp32(fftseg_plan p)
 {
     const int ln = p->log_n;
-    if (p->flags & (FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_LANES | FFTSEG_FLAG_FOURSTEP_TILES))
+    if (p->flags & (FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_WARP_LINES | FFTSEG_FLAG_FOURSTEP_TILES))
         return build_fourstep(p);
     const bool force2 = (p->flags & FFTSEG_FLAG_FORCE_TWOPASS) && ln >= 8;
     int rc;
@@ -423,14 +428,28 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 int encode_tmap_3d_swz(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
                        int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, int swizzle_bytes)
 {
+    const int64_t dims[3] = {d0, d1, d2};
+    const int64_t strides[2] = {stride1_bytes, stride2_bytes};
+    const uint32_t box[3] = {box0, box1, 1};
+    return encode_tmap(m, base, 3, dims, strides, box, elem_bytes, swizzle_bytes);
+}
+
+int encode_tmap(CUtensorMap *m, const void *base, int rank, const int64_t *dims_in, const int64_t *strides_in,
+                const uint32_t *box_in, int elem_bytes, int swizzle_bytes)
+{
+    if (rank < 1 || rank > 5) return set_error(FFTSEG_E_INVALID, "tensor map rank %d", rank);
+    cuuint64_t dims[5], strides[4];
+    cuuint32_t box[5], estr[5];
+    for (int i = 0; i < rank; ++i) {
+        dims[i] = (cuuint64_t)dims_in[i];
+        box[i] = (cuuint32_t)box_in[i];
+        estr[i] = 1;
+        if (i + 1 < rank) strides[i] = (cuuint64_t)strides_in[i];
+    }
     const CUtensorMapSwizzle swz = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
                                    : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                    : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
                                                          : CU_TENSOR_MAP_SWIZZLE_NONE;
-    const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
-    const cuuint64_t strides[2] = {(cuuint64_t)stride1_bytes, (cuuint64_t)stride2_bytes};
-    const cuuint32_t box[3] = {box0, box1, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
     // the driver entry point is looked up through the runtime, so the library
     // does not link libcuda and loads on machines without a GPU driver
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -442,10 +461,9 @@ int encode_tmap_3d_swz(CUtensorMap *m, const void *base, int64_t d0, int64_t d1,
             return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    CUresult r = encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64, 3,
-                        const_cast<void *>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+    CUresult r = encode(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32 : CU_TENSOR_MAP_DATA_TYPE_UINT64,
+                        (cuuint32_t)rank, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return FFTSEG_OK;
@@ -733,9 +751,13 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 const int64_t slabs = (int64_t)p->ring_nr * cs;
                 int rc = encode_tmap_3d_swz(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, (uint32_t)pwa, 256, 8,
                                             (int)(pwa * 8));
-                if (rc == FFTSEG_OK)
-                    rc = encode_tmap_3d_swz(&a.tmB, p->ring, n1, n2, slabs, n1 * 8, n * 8, (uint32_t)pwb, 256, 8,
-                                            (int)(pwb * 8));
+                if (rc == FFTSEG_OK) {
+                    // ring blocks [slab][k1 / wb][j2][k1 mod wb]
+                    const int64_t dims[4] = {wb, n2, n1 / wb, slabs};
+                    const int64_t strides[3] = {wb * 8, n2 * wb * 8, n * 8};
+                    const uint32_t box[4] = {(uint32_t)pwb, 256, 1, 1};
+                    rc = encode_tmap(&a.tmB, p->ring, 4, dims, strides, box, 8, (int)(pwb * 8));
+                }
                 if (rc == FFTSEG_OK)
                     rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8,
                                             (int)(pwb * 8));
@@ -752,6 +774,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 a.cs = cs;
                 a.nr = p->ring_nr;
                 a.la = p->wl_la;
+                a.stall = (p->flags & FFTSEG_FLAG_TEST_STALL) ? 1 : 0;
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
                 e = launch_fourstep_wl(p->log_n, sign, a, st);

@@ -94,10 +94,14 @@ int encode_tmap_3d(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int
 // aligned to the swizzle pattern's repeat (8 rows of the swizzle span).
 int encode_tmap_3d_swz(CUtensorMap *m, const void *base, int64_t d0, int64_t d1, int64_t d2, int64_t stride1_bytes,
                        int64_t stride2_bytes, uint32_t box0, uint32_t box1, int elem_bytes, int swizzle_bytes);
+// Any rank (1..5): dims[rank] (innermost first), byte strides of dims 1..rank-1,
+// box[rank], the swizzle as above.
+int encode_tmap(CUtensorMap *m, const void *base, int rank, const int64_t *dims, const int64_t *strides,
+                const uint32_t *box, int elem_bytes, int swizzle_bytes);
 
 // Plan flags that select a schedule (the rest are options).
 constexpr unsigned kPathFlags = FFTSEG_FLAG_FORCE_TWOPASS | FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_PRODUCER |
-                                FFTSEG_FLAG_FOURSTEP_LANES | FFTSEG_FLAG_FOURSTEP_TILES | FFTSEG_FLAG_CLUSTER_LOG2(0xF);
+                                FFTSEG_FLAG_FOURSTEP_WARP_LINES | FFTSEG_FLAG_FOURSTEP_TILES | FFTSEG_FLAG_CLUSTER_LOG2(0xF);
 
 // Autotuner (tune.cu): the schedule flags of the fastest schedule for n on
 // the current GPU, timed on min(batch, 256 MiB of input) segments.

@@ -88,8 +88,10 @@ std::vector<unsigned> candidates(int log_n, int prec)
             c.push_back(FFTSEG_FLAG_CLUSTER_LOG2(lc));
     }
     if (log_n >= 14) {
-        c.push_back(FFTSEG_FLAG_FOURSTEP_L2);
+        c.push_back(FFTSEG_FLAG_FOURSTEP_L2);  // the lane- or warp-line kernel where one applies
         c.push_back(FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_PRODUCER);
+        c.push_back(FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_TILES);
+        if (log_n == 16) c.push_back(FFTSEG_FLAG_FOURSTEP_L2 | FFTSEG_FLAG_FOURSTEP_WARP_LINES);
     }
     c.push_back(FFTSEG_FLAG_FORCE_TWOPASS);
     return c;

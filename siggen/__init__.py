@@ -17,6 +17,7 @@ LIB = os.path.join(HERE, "libsiggen.so")
 
 KIND_UNIFORM = 0
 KIND_TONES = 1
+KIND_POOL = 2
 DEFAULT_TONES = 32
 DEFAULT_SIGMA = 0.1
 
@@ -25,7 +26,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
+    subprocess.run(["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                     "-o", tmp, SRC, "-lm"], check=True)
     os.replace(tmp, LIB)
     return LIB
@@ -36,7 +37,7 @@ class Source(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("ntones", ctypes.c_int32), ("seed", ctypes.c_uint64),
                 ("sigma", ctypes.c_double), ("total_bytes", ctypes.c_int64),
                 ("nthreads", ctypes.c_int32), ("fail_at_call", ctypes.c_int32),
-                ("calls", ctypes.c_int64)]
+                ("calls", ctypes.c_int64), ("pool", ctypes.c_void_p), ("pool_bytes", ctypes.c_int64)]
 
 
 class Sink(ctypes.Structure):
@@ -128,7 +129,16 @@ def tone_params(seed: int, ntones: int = DEFAULT_TONES):
 def source(kind: int, seed: int, total_bytes: int, nthreads: int = None,
            ntones: int = DEFAULT_TONES, sigma: float = DEFAULT_SIGMA, fail_at_call: int = -1) -> Source:
     return Source(kind=kind, ntones=ntones, seed=seed, sigma=sigma, total_bytes=total_bytes,
-                  nthreads=_threads(nthreads), fail_at_call=fail_at_call, calls=0)
+                  nthreads=_threads(nthreads), fail_at_call=fail_at_call, calls=0, pool=None, pool_bytes=0)
+
+
+def pool_source(pool_ptr: int, pool_bytes: int, total_bytes: int, nthreads: int = None,
+                fail_at_call: int = -1) -> Source:
+    """A reader context over a pre-generated host buffer (pool_bytes, a multiple
+    of 8), read cyclically: byte offset b of the signal is pool[b mod pool_bytes]."""
+    return Source(kind=KIND_POOL, ntones=0, seed=0, sigma=0.0, total_bytes=total_bytes,
+                  nthreads=_threads(nthreads), fail_at_call=fail_at_call, calls=0, pool=pool_ptr,
+                  pool_bytes=pool_bytes)
 
 
 def sink(buf=None, fail_at_call: int = -1) -> Sink:

@@ -21,15 +21,23 @@
  *             a_k   = 10^(-3 u)          log-uniform on [1e-3, 1]
  *             Phi_k = h(kT, 3k+2)        initial phase * 2^64
  *             theta_k(t) = (F_k t + Phi_k) mod 2^64   (exact integer phase)
- *           Within each aligned block of 64 samples the exponential starts
- *           from the exact phase of the block's first sample and advances by
- *           complex multiplication with exp(2 pi i F_k 2^-64), in double.
+ *           In each aligned block of 64 samples starting at tb, sample
+ *           tb + m takes the product of two exact phasors, both evaluated by
+ *           cos and sin in double: that of the block's first sample,
+ *           (F_k tb + Phi_k) mod 2^64, and that of the offset, (F_k m) mod
+ *           2^64 (a table of 64 per tone).  The tones are thus independent
+ *           lanes over the block's samples, with no recurrence.
  *           Noise: Box-Muller in double from two uniform counters.
- *           The double sum is rounded once to float32.
+ *           The double sum (noise, then the tones in order) is rounded once
+ *           to float32.
+ *  pool     a pre-generated host buffer read cyclically (offset mod its
+ *           size), copied by several threads: a host-resident source that
+ *           leaves the generator out of a streaming measurement.
  *
  * Built with floating-point contraction off so that both host architectures
  * evaluate the same expression tree.
  */
+#define _GNU_SOURCE
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
@@ -80,7 +88,8 @@ typedef struct {
     int ntones;
     double sigma;
     uint64_t F[MAX_TONES], Phi[MAX_TONES];
-    double a[MAX_TONES], rr[MAX_TONES], ri[MAX_TONES];
+    double a[MAX_TONES];
+    double pr[MAX_TONES][BLOCK], pi[MAX_TONES][BLOCK]; /* exp(2 pi i ((F_k m) mod 2^64) 2^-64), m < BLOCK */
     uint64_t kA, kB;
 } tones_t;
 
@@ -93,9 +102,11 @@ static void tones_init(tones_t *tp, uint64_t seed, int ntones, double sigma)
         tp->F[k] = h(kT, 3 * (uint64_t)k);
         tp->a[k] = pow(10.0, -3.0 * u01(h(kT, 3 * (uint64_t)k + 1)));
         tp->Phi[k] = h(kT, 3 * (uint64_t)k + 2);
-        const double step = kTwoPi * u01(tp->F[k]);
-        tp->rr[k] = cos(step);
-        tp->ri[k] = sin(step);
+        for (int m = 0; m < BLOCK; ++m) {
+            const double ang = kTwoPi * u01(tp->F[k] * (uint64_t)m); /* mod 2^64 */
+            tp->pr[k][m] = cos(ang);
+            tp->pi[k][m] = sin(ang);
+        }
     }
     tp->kA = stream_key(seed, STREAM_NOISE_A);
     tp->kB = stream_key(seed, STREAM_NOISE_B);
@@ -104,26 +115,29 @@ static void tones_init(tones_t *tp, uint64_t seed, int ntones, double sigma)
 /* all BLOCK samples of the aligned block starting at tb */
 static void tones_block(const tones_t *tp, uint64_t tb, double *re, double *im)
 {
-    for (int m = 0; m < BLOCK; ++m) {
-        const uint64_t t = tb + (uint64_t)m;
-        const double u1 = ((double)(h(tp->kA, t) >> 11) + 1.0) * 0x1.0p-53; /* (0, 1] */
-        const double u2 = u01(h(tp->kB, t));
-        const double r = sqrt(-2.0 * log(u1));
-        re[m] = tp->sigma * r * cos(kTwoPi * u2);
-        im[m] = tp->sigma * r * sin(kTwoPi * u2);
+    if (tp->sigma != 0.0) {
+        for (int m = 0; m < BLOCK; ++m) {
+            const uint64_t t = tb + (uint64_t)m;
+            const double u1 = ((double)(h(tp->kA, t) >> 11) + 1.0) * 0x1.0p-53; /* (0, 1] */
+            const double u2 = u01(h(tp->kB, t));
+            const double r = sqrt(-2.0 * log(u1));
+            double sn, cs;
+            sincos(kTwoPi * u2, &sn, &cs);
+            re[m] = tp->sigma * r * cs;
+            im[m] = tp->sigma * r * sn;
+        }
+    } else {
+        for (int m = 0; m < BLOCK; ++m) re[m] = im[m] = 0.0;
     }
     for (int k = 0; k < tp->ntones; ++k) {
         const uint64_t theta = tp->F[k] * tb + tp->Phi[k]; /* mod 2^64 */
-        const double ang = kTwoPi * u01(theta);
-        double zr = tp->a[k] * cos(ang), zi = tp->a[k] * sin(ang);
-        const double rr = tp->rr[k], ri = tp->ri[k];
+        double sn, cs;
+        sincos(kTwoPi * u01(theta), &sn, &cs);
+        const double zr = tp->a[k] * cs, zi = tp->a[k] * sn;
+        const double *pr = tp->pr[k], *pi = tp->pi[k];
         for (int m = 0; m < BLOCK; ++m) {
-            re[m] += zr;
-            im[m] += zi;
-            const double nr = zr * rr - zi * ri;
-            const double ni = zr * ri + zi * rr;
-            zr = nr;
-            zi = ni;
+            re[m] += zr * pr[m] - zi * pi[m];
+            im[m] += zr * pi[m] + zi * pr[m];
         }
     }
 }
@@ -251,7 +265,55 @@ typedef struct {
     int32_t nthreads;
     int32_t fail_at_call; /* >= 0: return -1 on that call index (fault injection) */
     int64_t calls;        /* updated by the reader */
+    const uint8_t *pool;  /* kind 2: the buffer read cyclically */
+    int64_t pool_bytes;   /* a multiple of 8 */
 } siggen_source;
+
+typedef struct {
+    uint8_t *dst;
+    const uint8_t *pool;
+    int64_t pool_bytes, off, bytes;
+} pool_work_t;
+
+static void *pool_copy(void *arg)
+{
+    pool_work_t *w = (pool_work_t *)arg;
+    int64_t done = 0;
+    while (done < w->bytes) {
+        const int64_t o = (w->off + done) % w->pool_bytes;
+        int64_t n = w->pool_bytes - o;
+        if (n > w->bytes - done) n = w->bytes - done;
+        memcpy(w->dst + done, w->pool + o, (size_t)n);
+        done += n;
+    }
+    return NULL;
+}
+
+static void pool_read(const siggen_source *src, int64_t off, uint8_t *dst, int64_t bytes)
+{
+    int nt = src->nthreads < 1 ? 1 : src->nthreads > 64 ? 64 : src->nthreads;
+    if (bytes < ((int64_t)nt << 22)) nt = (int)(bytes >> 22) + 1; /* at least 4 MiB a thread */
+    pool_work_t w[64];
+    pthread_t tid[64];
+    int started = 0;
+    for (int i = 0; i < nt; ++i) {
+        int64_t b = bytes * i / nt, e = bytes * (i + 1) / nt;
+        b -= b % 64;
+        if (i + 1 < nt) e -= e % 64;
+        w[i].dst = dst + b;
+        w[i].pool = src->pool;
+        w[i].pool_bytes = src->pool_bytes;
+        w[i].off = off + b;
+        w[i].bytes = e - b;
+    }
+    for (int i = 1; i < nt; ++i) {
+        if (pthread_create(&tid[i], NULL, pool_copy, &w[i]) != 0) break;
+        started = i;
+    }
+    pool_copy(&w[0]);
+    for (int i = started + 1; i < nt; ++i) pool_copy(&w[i]);
+    for (int i = 1; i <= started; ++i) pthread_join(tid[i], NULL);
+}
 
 int64_t siggen_read(void *ctx, int64_t byte_offset, void *dst, int64_t bytes)
 {
@@ -264,6 +326,11 @@ int64_t siggen_read(void *ctx, int64_t byte_offset, void *dst, int64_t bytes)
     bytes -= bytes % 8;
     const int64_t t0 = byte_offset / 8, count = bytes / 8;
     int rc;
+    if (src->kind == 2) {
+        if (!src->pool || src->pool_bytes <= 0 || src->pool_bytes % 8) return -1;
+        pool_read(src, byte_offset, (uint8_t *)dst, bytes);
+        return bytes;
+    }
     if (src->kind == 0)
         rc = siggen_uniform_c64(src->seed, t0, count, (float *)dst, src->nthreads);
     else

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 import siggen
-from tests._util import rel_l2
+from tests._util import check_guard, guard, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +34,13 @@ def tol_blue(n):
 
 
 def run(plan, x):
-    y = plan.exec(torch.from_numpy(x).cuda())
+    d = torch.from_numpy(x).cuda()
+    dt = torch.float32 if plan.out_kind == fs.OUT_POWER else torch.complex64
+    buf, y = guard(torch.empty(d.shape, dtype=dt, device="cuda"))  # canaries past the output's end
+    plan.exec(d, out=y)
     torch.cuda.synchronize()
     plan.check()
+    check_guard(buf)
     return y.cpu().numpy()
 
 

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import siggen
-from tests._util import rel_l2, tol_fp32, tol_power
+from tests._util import check_guard, guard, rel_l2, tol_fp32, tol_power
 
 pytestmark = pytest.mark.gpu
 
@@ -35,9 +35,12 @@ def nseg_for(n, target=1 << 20):
 
 def run(plan, x_np, nseg=None):
     x = torch.from_numpy(x_np).cuda()
-    y = plan.exec(x, nseg=nseg)
+    dt = torch.float32 if plan.out_kind == fs.OUT_POWER else torch.complex64
+    buf, y = guard(torch.empty(x.shape, dtype=dt, device="cuda"))  # canaries past the output's end
+    plan.exec(x, out=y, nseg=nseg)
     torch.cuda.synchronize()
     plan.check()  # no kernel gave up a bounded wait
+    check_guard(buf)
     return y.cpu().numpy()
 
 
@@ -104,7 +107,7 @@ def test_warp_line_fourstep_65536_cycles_ring_in_place(direction, norm):
     # segments cycle the 3-chunk ring more than twice and end in a partial chunk
     n, B = 1 << 16, 230
     x = siggen.tones(881, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2)
+    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_FOURSTEP_L2 | fs.FLAG_FOURSTEP_WARP_LINES)
     assert plan.info()["path"] == "four-step"
     got = run(plan, x)
     sample = np.r_[0:2, 95:98, B - 2:B]

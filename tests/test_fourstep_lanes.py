@@ -1,5 +1,5 @@
 """GPU parity of the lane-line persistent four-step kernel (n = 2^16..2^20,
-FP32, complex output; the default at 2^17..2^20) against the FP64 oracle,
+FP32, complex output; the default there) against the FP64 oracle,
 per segment, on batches that cycle its ring of chunk buffers and end in a
 partial chunk; plus in-place runs and run-to-run bit equality (its tiles come
 from a queue, so CTAs take different tiles each run, but a tile's arithmetic
@@ -27,15 +27,14 @@ def built():
 
 
 def plan_for(n, B, direction, norm):
-    flags = fs.FLAG_FOURSTEP_LANES if n == 1 << 16 else 0
-    plan = fs.Plan(n, B, direction, norm, flags=flags)
+    plan = fs.Plan(n, B, direction, norm)
     assert plan.info()["path"] == "four-step"
     return plan
 
 
-# segments per 16 MiB chunk: 32, 16, 8, 4, 2; the batches span 4..7 chunks
-# (the ring holds 3), the last one partial
-@pytest.mark.parametrize("log_n,B", [(16, 101), (17, 61), (18, 29), (19, 15), (20, 13)])
+# segments per 32 MiB chunk (the default): 64, 32, 16, 8, 4; the batches span
+# 5 chunks (the ring holds 3), the last one partial
+@pytest.mark.parametrize("log_n,B", [(16, 293), (17, 139), (18, 69), (19, 35), (20, 17)])
 @pytest.mark.parametrize("direction,norm", [(FWD, fs.NORM_NONE), (INV, fs.NORM_BACKWARD), (FWD, fs.NORM_ORTHO)])
 def test_lane_line_fourstep_matches_oracle(log_n, B, direction, norm):
     n = 1 << log_n
@@ -78,9 +77,50 @@ def test_lane_line_fourstep_round_trip_and_partial_batches():
         assert (got[k:] == np.complex64(complex(7.0, 7.0))).all()  # untouched past nseg
 
 
-def test_lane_line_flag_refused_where_it_does_not_apply():
+def test_warp_line_flag_refused_where_it_does_not_apply():
     with pytest.raises(fs.FFTSegError) as e:
-        fs.Plan(1 << 21, 2, FWD, flags=fs.FLAG_FOURSTEP_LANES)
+        fs.Plan(1 << 17, 2, FWD, flags=fs.FLAG_FOURSTEP_WARP_LINES)
     assert e.value.status == fs.E_UNSUPPORTED
     with pytest.raises(fs.FFTSegError):
-        fs.Plan(1 << 18, 2, FWD, out_kind=fs.OUT_POWER, flags=fs.FLAG_FOURSTEP_LANES)
+        fs.Plan(1 << 16, 2, FWD, out_kind=fs.OUT_POWER, flags=fs.FLAG_FOURSTEP_WARP_LINES)
+
+
+@pytest.mark.parametrize("log_n", [16, 20])
+def test_lane_line_fourstep_small_chunks_cycle_the_ring(log_n, monkeypatch):
+    # 1 MiB chunks and two chunks of lookahead (a ring of four chunks): the
+    # batch cycles the ring many times, so column tiles wait on row tiles often
+    monkeypatch.setenv("FFTSEG_WL_CHUNK_MB", "1")
+    monkeypatch.setenv("FFTSEG_WL_LOOKAHEAD", "2")
+    n = 1 << log_n
+    B = 45 if log_n == 16 else 11
+    x = siggen.tones(1660 + log_n, B * n).reshape(B, n)
+    plan = plan_for(n, B, FWD, fs.NORM_NONE)
+    assert plan.info()["work_segs"] == max(1, (1 << 20) // (8 * n))
+    got = run_once(plan, x)
+    assert rel_l2(got, oracle.fft(x)) <= tol_fp32(n)
+
+
+def run_once(plan, x):
+    y = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    return y.cpu().numpy()
+
+
+def test_a_dependency_that_never_arrives_ends_in_a_timeout_status():
+    # the row tiles of segment 0 wait (with a short limit) for a column-tile
+    # count that is never reached: the kernel must give the wait up, complete,
+    # and report it through fftseg_plan_check; the plan then works again
+    n, B = 1 << 17, 40
+    x = torch.from_numpy(siggen.uniform(1670, B * n).reshape(B, n)).cuda()
+    stalled = fs.Plan(n, B, FWD, flags=fs.FLAG_TEST_STALL)
+    y = stalled.exec(x)
+    torch.cuda.synchronize()
+    with pytest.raises(fs.FFTSegError) as e:
+        stalled.check()
+    assert e.value.status == fs.E_TIMEOUT
+    stalled.check()  # the flag was cleared by the check that reported it
+    ref = plan_for(n, B, FWD, fs.NORM_NONE).exec(x)
+    torch.cuda.synchronize()
+    # every segment but the first had its dependencies; they are exact
+    np.testing.assert_array_equal(y[1:].cpu().numpy(), ref[1:].cpu().numpy())

@@ -52,6 +52,48 @@ def test_tones_follow_their_definition():
     assert np.max(np.abs(x - ref)) < 1e-5 * np.max(np.abs(ref))
 
 
+def _mix64(z):
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def test_tones_and_noise_to_float32_rounding():
+    # the whole sample against its definition evaluated independently in numpy
+    # (SplitMix64 counters, exact integer phases, Box-Muller), rounded once to
+    # float32: at most one float32 ulp apart (the two double evaluations
+    # differ only in their last bits)
+    seed, ntones, sigma = 2, 32, 0.1
+    G = np.uint64(0x9E3779B97F4A7C15)
+    key = lambda stream: _mix64(_mix64(np.uint64(seed)) + np.uint64(stream) * G)
+    F, Phi, a = siggen.tone_params(seed, ntones)
+    t = np.arange(123_456, 123_456 + 700, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        u1 = ((_mix64(key(2) + (t + np.uint64(1)) * G) >> np.uint64(11)).astype(np.float64) + 1.0) * 2.0 ** -53
+        u2 = (_mix64(key(3) + (t + np.uint64(1)) * G) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        ref = sigma * np.sqrt(-2.0 * np.log(u1)) * np.exp(2j * np.pi * u2)
+        for k in range(ntones):
+            frac = ((F[k] * t + Phi[k]) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+            ref = ref + a[k] * np.exp(2j * np.pi * frac)
+    x = siggen.tones(seed, t.size, t0=int(t[0]), ntones=ntones, sigma=sigma)
+    for part in ("real", "imag"):
+        got = getattr(x, part).astype(np.float64)
+        want = getattr(ref, part)
+        ulp = np.spacing(np.abs(want).astype(np.float32)).astype(np.float64)
+        assert np.all(np.abs(got - want) <= ulp + 1e-15), part
+
+
+def test_pool_source_reads_cyclically():
+    import ctypes
+    L = siggen.lib()
+    pool = siggen.uniform(4, 5000)
+    src = siggen.pool_source(pool.ctypes.data, pool.nbytes, total_bytes=3 * pool.nbytes, nthreads=3)
+    buf = np.empty(7000, dtype=np.complex64)
+    assert L.siggen_read(ctypes.byref(src), 4000 * 8, buf.ctypes.data, buf.nbytes) == buf.nbytes
+    want = np.concatenate([pool, pool, pool])[4000:11000]
+    np.testing.assert_array_equal(buf, want)
+
+
 def test_noise_statistics():
     x = siggen.tones(9, 1 << 18, ntones=0, sigma=0.1).astype(np.complex128)
     assert abs(np.std(x.real) - 0.1) < 0.002 and abs(np.std(x.imag) - 0.1) < 0.002
