@@ -133,7 +133,8 @@ cudaError_t block_frames_launch(const FramesBlockArgs &a, cudaStream_t st)
     using B = BlockShape<LOG_L>;
     constexpr size_t smem = (size_t)(B::SLOTS + 2 * B::E) * sizeof(float2) + 2 * sizeof(uint64_t);
     auto k = k_block_frames<LOG_L, BULK>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;

@@ -21,7 +21,8 @@ cudaError_t cluster_t(const ClusterArgs &a, cudaStream_t st)
     cfg.stream = st;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    static int max_clusters = 0;
+    static int max_clusters_dev[kMaxDevices] = {};  // per instantiation and device
+    int &max_clusters = max_clusters_dev[current_device_slot()];
     if (max_clusters == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         if (e != cudaSuccess) return e;

@@ -13,7 +13,8 @@ cudaError_t fourstep_t(const FourStepArgs &a, cudaStream_t st)
 {
     using Sh = FourStepShape<LOG_N1, LOG_N2, LOG_E>;
     auto k = k_fourstep<LOG_N1, LOG_N2, LOG_E, S, PREC>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         if (e != cudaSuccess) return e;
@@ -52,7 +53,8 @@ cudaError_t fourstep_hw_t(const FourStepHwArgs &a, cudaStream_t st)
 {
     using Sh = FourStepHwShape;
     auto k = k_fourstep_hw<S>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         if (e != cudaSuccess) return e;
@@ -75,7 +77,8 @@ cudaError_t fourstep_ws_t(const FourStepWsArgs &a, cudaStream_t st)
 {
     using Sh = FourStepWsShape<LOG_N1, LOG_N2, LOG_E>;
     auto k = k_fourstep_ws<LOG_N1, LOG_N2, LOG_E, S>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::SMEM);
         if (e != cudaSuccess) return e;

@@ -6,17 +6,18 @@ namespace fftseg {
 
 namespace {
 
-int g_sm_count = 0;
+int g_sm_count[kMaxDevices] = {};
 
 int sm_count()
 {
-    if (g_sm_count == 0) {
+    int &c = g_sm_count[current_device_slot()];
+    if (c == 0) {
         int dev = 0, v = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        g_sm_count = v > 0 ? v : 1;
+        c = v > 0 ? v : 1;
     }
-    return g_sm_count;
+    return c;
 }
 
 template <int LOG_L, int S, int PREC = PREC_FP32>
@@ -24,7 +25,8 @@ cudaError_t block_t(const BlockArgs &a, cudaStream_t st)
 {
     using B = BlockShape<LOG_L>;
     auto k = k_block<LOG_L, S, PREC>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
         if (e != cudaSuccess) return e;

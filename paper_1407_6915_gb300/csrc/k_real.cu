@@ -173,7 +173,8 @@ cudaError_t block_r2c_t(const RealBlockArgs &a, cudaStream_t st)
 {
     using B = BlockShape<LOG_L>;
     auto k = k_block_r2c<LOG_L>;
-    static int per_sm = 0;
+    static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
+    int &per_sm = per_sm_dev[current_device_slot()];
     if (per_sm == 0) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B::SMEM);
         if (e != cudaSuccess) return e;

@@ -7,6 +7,16 @@
 
 namespace fftseg {
 
+// Launch-shape caches (occupancy, SM count) are kept per device: index of
+// the current device into such a cache (devices past the last slot share it).
+constexpr int kMaxDevices = 64;
+inline int current_device_slot()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    return dev < kMaxDevices ? dev : kMaxDevices - 1;
+}
+
 // Single-pass segment-major tiles for n = 2^log_n <= 4096 (persistent CTAs,
 // a.ntiles tiles of block_segments_per_cta segments).  Returns the launch error.
 // prec: PREC_FP32, or PREC_FP16 / PREC_BF16 (tensor-core radix-16 stages, n = 16, 256, 4096).
@@ -42,9 +52,11 @@ cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t s
 // output): lines of 256..1024 points with 32 points per lane, a queue of
 // column and row tiles, loader and retirer warps, swizzled TMA tiles.
 struct FourStepWlArgs;
-cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st);
-// Factorisation n = N1 x N2 and tile size E of the lane-line kernel.
-bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e);
+// Tiles of 2^log_e points: 13 (one CTA per SM) or 12 (two CTAs per SM).
+cudaError_t launch_fourstep_wl(int log_n, int log_e, int sign, const FourStepWlArgs &a, cudaStream_t st);
+// Factorisation n = N1 x N2 of the lane-line kernel (false: not built for
+// this length and tile size).
+bool fourstep_wl_shape(int log_n, int log_e, int *log_n1, int *log_n2);
 // Real-signal segments (k_real.cu): the pass between a length-n real DFT and
 // the length-m = n/2 complex DFT.  post: complex FFT output [nseg][m] -> the
 // n/2 + 1 bins [nseg][m + 1] (complex64, or float32 |X|^2 with power); pre:

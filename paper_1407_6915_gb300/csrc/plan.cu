@@ -190,8 +190,10 @@ int env_int(const char *name, int dflt, int lo, int hi)
 // column passes are tuning knobs read at plan creation.
 int build_fourstep_wl(fftseg_plan p)
 {
-    int l1, l2, le;
-    if (!fourstep_wl_shape(p->log_n, &l1, &l2, &le)) return set_error(FFTSEG_E_UNSUPPORTED, "lane-line shape");
+    int l1, l2;
+    const int le = env_int("FFTSEG_WL_TILE_LOG2", 13, 12, 13);
+    if (!fourstep_wl_shape(p->log_n, le, &l1, &l2)) return set_error(FFTSEG_E_UNSUPPORTED, "lane-line shape");
+    p->wl_log_e = le;
     p->path = PATH_FOURSTEP;
     p->log_n1 = l1;
     p->log_n2 = l2;
@@ -344,11 +346,15 @@ int build_fp32(fftseg_plan p)
     int l1, l2, lc;
     const int want_c = (int)((p->flags >> 8) & 0xFu);
     // measured on GB300: the cluster path wins up to 2^15 (and for |X|^2
-    // output at 2^16), the persistent four-step above: at 2^16 its
-    // warp-local-line kernel (16384 segments: 4.3 ms against 5.5 ms for
-    // 16-CTA clusters, whose all-to-all exchange is bound by the SM-to-SM
-    // network), from 2^17 on because a 16-CTA cluster per segment leaves SMs idle
-    if (!force2 && want_c == 0 && (ln >= 17 || (ln == 16 && p->out_kind == FFTSEG_OUT_COMPLEX)))
+    // output at 2^16), the persistent four-step above: at 2^16 its lane-line
+    // kernel (16384 segments: 4.14 ms against 5.5 ms for 16-CTA clusters,
+    // whose all-to-all exchange is bound by the SM-to-SM network), from 2^17
+    // on because a 16-CTA cluster per segment leaves SMs idle
+    // (at 2^24 with complex output the two-pass path measured 8 % faster than
+    // the persistent four-step: a segment's 128 MiB intermediate cannot stay
+    // in L2, so both make two HBM passes)
+    const bool twopass_24 = ln == 24 && p->out_kind == FFTSEG_OUT_COMPLEX;
+    if (!force2 && want_c == 0 && !twopass_24 && (ln >= 17 || (ln == 16 && p->out_kind == FFTSEG_OUT_COMPLEX)))
         return build_fourstep(p);
     if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: no cluster of 2^%d CTAs is built for n=2^%d",
@@ -777,7 +783,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 a.stall = (p->flags & FFTSEG_FLAG_TEST_STALL) ? 1 : 0;
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
-                e = launch_fourstep_wl(p->log_n, sign, a, st);
+                e = launch_fourstep_wl(p->log_n, p->wl_log_e, sign, a, st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
                 count_launches(1);
                 return FFTSEG_OK;
