@@ -597,17 +597,19 @@ def file_bench():
 
 
 def bluestein_bench(peak):
-    """Lengths that are not powers of two (Bluestein over M = 2^ceil(log2(2n - 1))
-    points): n = 1000 and the prime 10007, 2^29 complex64 samples (4 GiB) each,
-    forward.  Algorithmic bytes: 16 per point, as for every length."""
+    """Lengths that are not powers of two, 2^29 complex64 samples (4 GiB)
+    each, forward: n = 1000 and 3000 on the mixed-radix path (the default for
+    lengths 2^a 3^b 5^c 7^d <= 4096), n = 1000 through Bluestein (M = 2048)
+    for comparison, and the prime 10007 through Bluestein (M = 32768).
+    Algorithmic bytes: 16 per point, as for every length."""
     import torch
     import paper_1407_6915_gb300 as fs
     import siggen
     rows = []
-    for n in (1000, 10007):
+    for n, flags in ((1000, 0), (3000, 0), (1000, fs.FLAG_BLUESTEIN), (10007, 0)):
         B = (1 << 29) // n
         x = torch.from_numpy(siggen.uniform(9, B * n)).cuda().view(B, n)
-        plan = fs.Plan(n, B, fs.FORWARD)
+        plan = fs.Plan(n, B, fs.FORWARD, flags=flags)
         y = torch.empty_like(x)
         for _ in range(2):
             plan.exec(x, out=y)
@@ -621,14 +623,16 @@ def bluestein_bench(peak):
         ms = e0.elapsed_time(e1) / 3
         # round trip through the inverse plan (1/n) against the input; parity
         # with the oracle's direct DFT is the tests' job
-        inv = fs.Plan(n, B, fs.INVERSE, fs.NORM_BACKWARD)
+        inv = fs.Plan(n, B, fs.INVERSE, fs.NORM_BACKWARD, flags=flags)
         z = inv.exec(y)
         torch.cuda.synchronize()
         inv.check()
         err = float(torch.linalg.vector_norm(z - x) / torch.linalg.vector_norm(x))
         del inv, z
         algo = 16.0 * n * B
-        rows.append({"n": n, "M": int(plan.info()["n1"]), "segments": B, "ms": round(ms, 4),
+        info = plan.info()
+        rows.append({"n": n, "path": info["path"], "M": int(info["n1"]) if info["path"] == "bluestein" else None,
+                     "segments": B, "ms": round(ms, 4),
                      "gflops": round(5.0 * n * math.log2(n) * B / (ms / 1e3) / 1e9, 1),
                      "gbs_algorithmic": round(algo / (ms / 1e3) / 1e9, 1),
                      "hbm_frac": round(algo / (ms / 1e3) / 1e9 / peak, 4),

@@ -103,6 +103,9 @@ enum { FFTSEG_WINDOW_RECT = 0, FFTSEG_WINDOW_HANN = 1 };
    returns FFTSEG_E_TIMEOUT.  Shows that a lost dependency ends in an error
    status, not a hang. */
 #define FFTSEG_FLAG_TEST_STALL 0x1000u
+/* lengths that are not powers of two: Bluestein's algorithm even where the
+   mixed-radix path applies (n = 2^a 3^b 5^c 7^d <= 4096) */
+#define FFTSEG_FLAG_BLUESTEIN 0x2000u
 
 #define FFTSEG_MAX_LOG2N 24
 

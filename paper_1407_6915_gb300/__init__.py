@@ -26,12 +26,13 @@ FLAG_AUTOTUNE = 0x10
 FLAG_REAL = 0x20
 FLAG_FOURSTEP_WARP_LINES, FLAG_FOURSTEP_TILES = 0x40, 0x80
 FLAG_TEST_STALL = 0x1000
+FLAG_BLUESTEIN = 0x2000
 FILE_DIRECT, FILE_KEEP = 0x1, 0x2
 
 
 WINDOW_RECT, WINDOW_HANN = 0, 1
 PATH_NAMES = {0: "block", 1: "cluster", 2: "two-pass", 3: "tensor-core", 4: "four-step", 5: "real",
-              6: "frames", 7: "bluestein"}
+              6: "frames", 7: "bluestein", 8: "mixed-radix"}
 
 OK, E_INVALID, E_NOMEM, E_CUDA, E_IO, E_PARTIAL, E_TIMEOUT, E_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 

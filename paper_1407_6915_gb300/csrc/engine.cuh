@@ -187,10 +187,67 @@ HDEV void dft32(float2 *v)
     }
 }
 
+// Odd prime radix R = 3, 5, 7 by the pair sums and differences of the
+// inputs: with A_k = v_k + v_{R-k}, B_k = v_k - v_{R-k} (k = 1..(R-1)/2),
+//   X_0 = v_0 + sum_k A_k,
+//   X_m, X_{R-m} = v_0 + sum_k cos(2 pi m k / R) A_k  +/-  sigma i sum_k sin(2 pi m k / R) B_k.
+// odd_cos / odd_sin give cos and sin(2 pi q / R) for q = m k mod R (cos is
+// even and sin odd in q, so q in 1..R-1 is enough).
+template <int R>
+HDEV constexpr float odd_cos(int q)
+{
+    // R = 3: cos(2 pi / 3); R = 5: cos(2 pi / 5), cos(4 pi / 5); R = 7: cos(2 pi k / 7), k = 1, 2, 3
+    const int r = q <= R / 2 ? q : R - q;
+    return R == 3 ? -0.5f
+           : R == 5 ? (r == 1 ? 0.30901699437494742410f : -0.80901699437494742410f)
+                    : (r == 1 ? 0.62348980185873353053f : r == 2 ? -0.22252093395631440429f : -0.90096886790241912624f);
+}
+template <int R>
+HDEV constexpr float odd_sin(int q)
+{
+    const int r = q <= R / 2 ? q : R - q;
+    const float v = R == 3 ? 0.86602540378443864676f
+                    : R == 5 ? (r == 1 ? 0.95105651629515357212f : 0.58778525229247312917f)
+                             : (r == 1 ? 0.78183148246802980871f : r == 2 ? 0.97492791218182360702f
+                                                                          : 0.43388373911755812048f);
+    return q <= R / 2 ? v : -v;
+}
+
+template <int R, int S>
+HDEV void dft_odd(float2 *v)
+{
+    constexpr int H = (R - 1) / 2;
+    float2 A[H], B[H];
+    float2 x0 = v[0];
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+        A[k] = cadd(v[k + 1], v[R - 1 - k]);
+        B[k] = csub(v[k + 1], v[R - 1 - k]);
+    }
+    float2 X0 = x0;
+#pragma unroll
+    for (int k = 0; k < H; ++k) X0 = cadd(X0, A[k]);
+#pragma unroll
+    for (int m = 0; m < H; ++m) {
+        float2 P = x0, Q = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+            const float c = odd_cos<R>(((m + 1) * (k + 1)) % R), sn = odd_sin<R>(((m + 1) * (k + 1)) % R);
+            P = make_float2(P.x + c * A[k].x, P.y + c * A[k].y);
+            Q = make_float2(Q.x + sn * B[k].x, Q.y + sn * B[k].y);
+        }
+        const float2 iQ = mul_si<S>(Q);  // sigma i Q
+        v[m + 1] = cadd(P, iQ);
+        v[R - 1 - m] = csub(P, iQ);
+    }
+    v[0] = X0;
+}
+
 template <int R, int S>
 HDEV void dft(float2 *v)
 {
     if constexpr (R == 2) dft2<S>(v[0], v[1]);
+    else if constexpr (R == 3 || R == 5 || R == 7) dft_odd<R, S>(v);
     else if constexpr (R == 4) dft4<S>(v[0], v[1], v[2], v[3]);
     else if constexpr (R == 8) dft8<S>(v);
     else if constexpr (R == 16) dft16<S>(v);

@@ -136,6 +136,25 @@ struct BlueBlockArgs {
     float scale;
 };
 cudaError_t launch_blue_block(int log_m, const BlueBlockArgs &a, cudaStream_t st);
+// Lengths n = 2^a 3^b 5^c 7^d <= 4096 (not powers of two) in one pass
+// (k_mixed.cu): mixed-radix Stockham stages over tiles of whole segments.
+constexpr int kMixMaxStages = 16;
+struct MixedArgs {
+    const float2 *in;   // [nseg][n] complex64
+    void *out;          // [nseg][n] complex64, or float32 |X|^2
+    const float2 *tw;   // stage twiddles: stage t at twoff[t], [r-1][k] = w_{ns R}^{k r}, k < ns
+    int *err;
+    int64_t nseg, ntiles;
+    int n, segs_per_tile, nstages, out_power;
+    int radix[kMixMaxStages], ns[kMixMaxStages], twoff[kMixMaxStages];
+    float rm[kMixMaxStages], rns[kMixMaxStages];  // 1 / (n / radix), 1 / ns
+    float scale;
+};
+cudaError_t launch_mixed(int sign, const MixedArgs &a, cudaStream_t st);
+// The radix schedule for n (odd radices 7, 5, 3 first, then 8s and one 4 or
+// 2); false if n has another prime factor or is too long for one tile.
+bool mixed_schedule(int64_t n, int *nstages, int *radix);
+int mixed_segments_per_tile(int64_t n);
 // Factorisation and tile widths used for n.
 bool fourstep_shape(int log_n, int *log_n1, int *log_n2, int *log_wa, int *log_wb);
 // The four-step twiddle w_n^{j2 k1} is the product of two table entries,

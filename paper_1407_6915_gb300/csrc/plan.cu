@@ -400,6 +400,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
         case PATH_FOURSTEP: return 1;
+        case PATH_MIXED: return 1;
         case PATH_BLUESTEIN: {
             if (blue_fused(p)) return 1;
             int64_t k = 0;
@@ -477,6 +478,34 @@ int encode_tmap(CUtensorMap *m, const void *base, int rank, const int64_t *dims_
 
 int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
 {
+    if (p->path == PATH_MIXED) {
+        MixedArgs a{};
+        const int spt = mixed_segments_per_tile(p->n);
+        a.in = static_cast<const float2 *>(d_in);
+        a.out = d_out;
+        a.tw = p->twA;
+        a.err = p->d_err;
+        a.nseg = nseg;
+        a.ntiles = (nseg + spt - 1) / spt;
+        a.n = (int)p->n;
+        a.segs_per_tile = spt;
+        a.nstages = p->mix_nstages;
+        a.out_power = p->out_kind == FFTSEG_OUT_POWER;
+        a.scale = p->scale;
+        int64_t ns = 1;
+        for (int t = 0; t < p->mix_nstages; ++t) {
+            a.radix[t] = p->mix_radix[t];
+            a.ns[t] = (int)ns;
+            a.twoff[t] = p->mix_twoff[t];
+            a.rm[t] = (float)(1.0 / (double)(p->n / p->mix_radix[t]));
+            a.rns[t] = (float)(1.0 / (double)ns);
+            ns *= p->mix_radix[t];
+        }
+        cudaError_t e = launch_mixed(p->direction, a, st);
+        if (e != cudaSuccess) return cuda_error(e, "mixed-radix kernel launch");
+        count_launches(1);
+        return FFTSEG_OK;
+    }
     if (p->path == PATH_BLUESTEIN && blue_fused(p)) {
         // M <= 4096: every row on chip from chirp-in to chirp-out, one launch
         BlueBlockArgs a{};
@@ -1052,6 +1081,59 @@ using namespace fftseg;
 
 extern "C" {
 
+// Lengths 2^a 3^b 5^c 7^d <= 4096 that are not powers of two: one pass of
+// mixed-radix Stockham stages (k_mixed.cu).  The stage twiddles
+// w_{Ns R}^{k r} are evaluated in double on the host and rounded once.
+int create_mixed(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int out_kind,
+                 unsigned flags, const int *radix, int nstages)
+{
+    fftseg_plan p = new (std::nothrow) fftseg_plan_s();
+    if (!p) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        return cuda_error(e, "cudaGetDevice");
+    }
+    p->n = n;
+    p->batch = batch;
+    p->log_n = 0;
+    p->direction = direction;
+    p->norm = norm;
+    p->precision = FFTSEG_PREC_FP32;
+    p->out_kind = out_kind;
+    p->flags = flags;
+    p->path = PATH_MIXED;
+    if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
+    else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
+    p->mix_nstages = nstages;
+    std::vector<float2> h;
+    int64_t ns = 1;
+    for (int t = 0; t < nstages; ++t) {
+        const int64_t R = radix[t];
+        p->mix_radix[t] = (int)R;
+        p->mix_twoff[t] = (int)h.size();
+        if (ns > 1) {
+            const size_t base = h.size();
+            h.resize(base + (size_t)((R - 1) * ns));
+            for (int64_t r = 1; r < R; ++r) host_roots(h.data() + base + (r - 1) * ns, ns, ns * R, r);
+        }
+        ns *= R;
+    }
+    if (h.empty()) h.push_back(make_float2(1.f, 0.f));
+    int rc = upload(&p->twA, h);
+    if (rc == FFTSEG_OK) {
+        e = cudaMalloc((void **)&p->d_err, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(status flag)");
+    }
+    if (rc != FFTSEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    *out = p;
+    return FFTSEG_OK;
+}
+
 int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm,
                        int precision, int out_kind, unsigned flags)
 {
@@ -1080,6 +1162,9 @@ int fftseg_plan_create(fftseg_plan *out, int64_t n, int64_t batch, int direction
     if (!is_pow2(n)) {
         if (precision != FFTSEG_PREC_FP32)
             return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: lengths that are not powers of two are FP32 only");
+        int radix[kMixMaxStages], nst = 0;
+        if (!(flags & FFTSEG_FLAG_BLUESTEIN) && mixed_schedule(n, &nst, radix))
+            return create_mixed(out, n, batch, direction, norm, out_kind, flags, radix, nst);
         return create_bluestein(out, n, batch, direction, norm, out_kind, flags);
     }
     if (flags & FFTSEG_FLAG_AUTOTUNE) {  // replace the schedule flags by the fastest measured schedule
@@ -1184,9 +1269,9 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
 {
     if (!p || !info) return set_error(FFTSEG_E_INVALID, "plan_info: NULL argument");
     info[0] = p->path;
-    info[1] = int64_t(1) << p->log_n1;
+    info[1] = p->path == PATH_MIXED ? p->n : int64_t(1) << p->log_n1;
     info[2] = (p->path == PATH_BLOCK || p->path == PATH_REAL || p->path == PATH_FRAMES ||
-               p->path == PATH_BLUESTEIN)
+               p->path == PATH_BLUESTEIN || p->path == PATH_MIXED)
                   ? 1
                   : int64_t(1) << p->log_n2;
     info[3] = p->path == PATH_BLUESTEIN ? (p->rwork ? p->rchunk * p->bm * 8 : 0)
@@ -1195,6 +1280,7 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
                                     : p->work ? p->work_segs * p->n * 8
                                               : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
     info[4] = (p->path == PATH_REAL || p->path == PATH_FRAMES || p->path == PATH_BLUESTEIN) ? p->rchunk
+              : p->path == PATH_MIXED ? mixed_segments_per_tile(p->n)
               : p->work ? p->work_segs : p->ring_cs;
     info[5] = launches_per_exec(p, p->batch);
     return FFTSEG_OK;

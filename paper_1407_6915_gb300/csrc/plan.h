@@ -19,7 +19,8 @@ enum Path {
     PATH_FOURSTEP = 4,
     PATH_REAL = 5,
     PATH_FRAMES = 6,
-    PATH_BLUESTEIN = 7
+    PATH_BLUESTEIN = 7,
+    PATH_MIXED = 8
 };
 
 }  // namespace fftseg
@@ -68,6 +69,10 @@ struct fftseg_plan_s {
     // M-point plans, the chirp and B = FFT_M(conjugate chirp) / M; rwork holds
     // a chunk of M-point rows
     fftseg_plan_s *inner2 = nullptr;
+    // lengths 2^a 3^b 5^c 7^d <= 4096 (mixed-radix path): the radix schedule
+    // (twA holds the stage twiddles, stage t at mix_twoff[t])
+    int mix_nstages = 0;
+    int mix_radix[16] = {}, mix_twoff[16] = {};
     float2 *bw = nullptr, *bhat = nullptr;
     int64_t bm = 0;
     // fftseg_stream phase split of the last call (ms)

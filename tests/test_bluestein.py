@@ -50,7 +50,7 @@ def run(plan, x):
 def test_bluestein_matches_direct_dft(n, direction, norm):
     B = 5
     x = siggen.tones(1300 + n, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, direction, norm)
+    plan = fs.Plan(n, B, direction, norm, flags=fs.FLAG_BLUESTEIN)
     assert plan.info()["path"] == "bluestein"
     got = run(plan, x)
     ref = oracle.dft(x, direction, norm)
@@ -62,7 +62,7 @@ def test_bluestein_chunks_and_large_n(n, B):
     # more segments than one chunk of M-point rows (and than one launch's grid
     # rows at n = 6), and lengths whose M reaches 2^23; bins spot-checked
     x = siggen.uniform(1400 + n, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, fs.FORWARD)
+    plan = fs.Plan(n, B, fs.FORWARD, flags=fs.FLAG_BLUESTEIN)
     got = run(plan, x)
     segs = np.r_[0, B // 2, B - 1]
     bins = np.unique(np.r_[0, 1, n // 3, n // 2, n - 1, np.arange(0, n, max(1, n // 7))])
@@ -73,7 +73,7 @@ def test_bluestein_chunks_and_large_n(n, B):
 def test_bluestein_power_and_stream():
     n, B = 3000, 40
     x = siggen.tones(1500, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, fs.FORWARD, out_kind=fs.OUT_POWER)
+    plan = fs.Plan(n, B, fs.FORWARD, out_kind=fs.OUT_POWER, flags=fs.FLAG_BLUESTEIN)
     got = run(plan, x)
     X = oracle.dft(x)
     assert rel_l2(got, X.real ** 2 + X.imag ** 2) <= 2 * tol_blue(n)
@@ -94,7 +94,7 @@ def test_bluestein_power_and_stream():
         chunks.append(off)
         return 0
 
-    sp = fs.Plan(n, 16, fs.FORWARD, out_kind=fs.OUT_POWER)
+    sp = fs.Plan(n, 16, fs.FORWARD, out_kind=fs.OUT_POWER, flags=fs.FLAG_BLUESTEIN)
     rc, committed = sp.stream(rd, None, wr, None, x.nbytes, 0, 16)
     assert rc == fs.OK and committed == x.nbytes and len(chunks) == 3
     np.testing.assert_array_equal(out.reshape(B, n), got)
@@ -109,7 +109,7 @@ def test_bluestein_fused_rows(n, B, out_kind):
     # goes through the five-pass chunks
     M = 1 << math.ceil(math.log2(2 * n - 1))
     x = siggen.tones(1600 + n, B * n).reshape(B, n)
-    plan = fs.Plan(n, B, fs.INVERSE, fs.NORM_ORTHO, out_kind=out_kind)
+    plan = fs.Plan(n, B, fs.INVERSE, fs.NORM_ORTHO, out_kind=out_kind, flags=fs.FLAG_BLUESTEIN)
     info = plan.info()
     if M <= 4096:
         assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0

@@ -1,4 +1,5 @@
-"""The kernels' in-register DFT butterflies (radix 2..32, both signs),
+"""The kernels' in-register DFT butterflies (radix 2, 3, 4, 5, 7, 8, 16, 32,
+both signs),
 compiled for the host from the same header the sm_103a kernels include and
 checked against the direct DFT in double: no GPU needed.  A wrong rotation
 constant or a dropped term in a butterfly shows up here before any kernel
@@ -46,6 +47,9 @@ int main() {
     printf("%d %.3e\n", 8, err<8, -1> () > err<8, 1>() ? err<8, -1>() : err<8, 1>());
     printf("%d %.3e\n", 16, err<16, -1>() > err<16, 1>() ? err<16, -1>() : err<16, 1>());
     printf("%d %.3e\n", 32, err<32, -1>() > err<32, 1>() ? err<32, -1>() : err<32, 1>());
+    printf("%d %.3e\n", 3, err<3, -1> () > err<3, 1>() ? err<3, -1>() : err<3, 1>());
+    printf("%d %.3e\n", 5, err<5, -1> () > err<5, 1>() ? err<5, -1>() : err<5, 1>());
+    printf("%d %.3e\n", 7, err<7, -1> () > err<7, 1>() ? err<7, -1>() : err<7, 1>());
     return 0;
 }
 '''
@@ -62,7 +66,7 @@ def test_register_butterflies_match_the_direct_dft(tmp_path):
                    check=True, capture_output=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
     errs = {int(a): float(b) for a, b in (line.split() for line in out if line.strip())}
-    assert set(errs) == {2, 4, 8, 16, 32}
+    assert set(errs) == {2, 3, 4, 5, 7, 8, 16, 32}
     for r, e in errs.items():
         # float32 butterflies: a few units in the last place of the largest output
         assert e < 4e-7 * max(1, r.bit_length()), (r, e)
