@@ -127,11 +127,27 @@ FDEV void wl_group_sync(int group)
     }
 }
 
+// The lane's stage-2 twiddles of an L-point line, w_L^{(j + P e) r} for
+// e < 32 / P, 1 <= r < P, at [e (P - 1) + r - 1] (held in registers when both
+// passes have the same line length).
+template <class PS>
+struct WlTw {
+    float2 w[PS::Q * (PS::P - 1)];
+    FDEV void load(const float2 *tab, int j)
+    {
+#pragma unroll
+        for (int e = 0; e < PS::Q; ++e)
+#pragma unroll
+            for (int r = 1; r < PS::P; ++r) w[e * (PS::P - 1) + r - 1] = tab[(r - 1) * 32 + j + PS::P * e];
+    }
+};
+
 // The DFT of the calling lane's line of a pass, in place in the tile buffer
 // at byte offset tb.  On return v[e * P + r] holds bin j + P e + 32 r.
-// tw: stage-2 twiddles in shared memory.
+// tw: stage-2 twiddles in shared memory, or (treg) the lane's own in registers.
 template <class PS, int S>
-FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int group, const float2 *tw)
+FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int group, const float2 *tw,
+                  const WlTw<PS> *treg = nullptr)
 {
     constexpr int P = PS::P, Q = PS::Q, ROWB = PS::ROWB;
     const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
@@ -156,7 +172,8 @@ FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int grou
 #pragma unroll
     for (int e = 0; e < Q; ++e) {
 #pragma unroll
-        for (int r = 1; r < P; ++r) v[e * P + r] = twmul<S>(v[e * P + r], tw[(r - 1) * 32 + j + P * e]);
+        for (int r = 1; r < P; ++r)
+            v[e * P + r] = twmul<S>(v[e * P + r], treg ? treg->w[e * (P - 1) + r - 1] : tw[(r - 1) * 32 + j + P * e]);
         dft<P, S>(v + e * P);
     }
 }
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
         // dependency, waits for a free buffer and issues the tile's TMA loads.
         const int lane = tid & 31;
         const int TA = a.cs * Sh::TSEG_A, TB = a.cs * Sh::TSEG_B;
-        const int64_t total = (int64_t)a.nchunks * (TA + TB);
+        const int total = a.nchunks * (TA + TB);  // < 2^31 (checked by the host)
         int *const doneA = a.ctr + 1;
         int *const doneB = a.ctr + 1 + (int64_t)a.nchunks * a.cs;
         const int64_t ring_segs = (int64_t)a.nr * a.cs;
@@ -287,17 +304,18 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
         const int full_groups = a.nchunks - lead;
         // Global order: A(0) .. A(LA-1), then for g = 0, 1, ...: A(g+LA) (while
         // it exists), B(g).  B(c) needs A(c); A(c) needs B(c - nr), nr >= LA + 2.
-        auto decode = [&](int64_t t, int &isb, int &c, int &w) {
-            if (t < (int64_t)lead * TA) {
+        // (32-bit arithmetic: the decode is on the loader's critical path)
+        auto decode = [&](int t, int &isb, int &c, int &w) {
+            if (t < lead * TA) {
                 isb = 0;
-                c = (int)(t / TA);
-                w = (int)(t % TA);
+                c = t / TA;
+                w = t - c * TA;
                 return;
             }
-            const int64_t t2 = t - (int64_t)lead * TA;
-            if (t2 < (int64_t)full_groups * (TA + TB)) {
-                const int g = (int)(t2 / (TA + TB));
-                const int x = (int)(t2 % (TA + TB));
+            const int t2 = t - lead * TA;
+            if (t2 < full_groups * (TA + TB)) {
+                const int g = t2 / (TA + TB);
+                const int x = t2 - g * (TA + TB);
                 if (x < TA) {
                     isb = 0;
                     c = g + LA;
@@ -309,14 +327,14 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                 }
                 return;
             }
-            const int64_t t3 = t2 - (int64_t)full_groups * (TA + TB);
+            const int t3 = t2 - full_groups * (TA + TB);
             isb = 1;
-            c = full_groups + (int)(t3 / TB);
-            w = (int)(t3 % TB);
+            c = full_groups + t3 / TB;
+            w = t3 - (t3 / TB) * TB;
         };
         int64_t a_seen = -1, b_seen = -1;  // highest segment whose column / row tiles were seen complete
         const uint64_t stream_policy = policy_evict_first();  // the input is read once
-        int64_t t = 0;
+        int t = 0;
         if (lane == 0) t = atomicAdd(a.ctr, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         for (int64_t m = 0;; ++m) {
@@ -324,6 +342,10 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             int isb = 0, c = 0, w = 0;
             int64_t s = 0;
             const bool end = t >= total;
+            // the next tile is taken now: the atomic's latency overlaps this
+            // tile's dependency probe, buffer wait and copies
+            int t_next = 0;
+            if (lane == 0 && !end) t_next = atomicAdd(a.ctr, 1);
             if (lane == 0 && !end) {
                 decode(t, isb, c, w);
                 s = (int64_t)c * a.cs + (isb ? w / Sh::TSEG_B : w / Sh::TSEG_A);
@@ -380,16 +402,23 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                         item[4 * b + 2] = isb ? -tile - 1 : tile;
                         mbar_arrive(&full[b]);
                     }
-                    t = atomicAdd(a.ctr, 1);  // the next tile, taken early
                 }
             }
-            t = __shfl_sync(0xffffffffu, t, 0);
+            t = __shfl_sync(0xffffffffu, t_next, 0);
             if (end) break;
         }
         return;
     }
 
     // ================================================================ compute
+    // with one line length for both passes a lane keeps the same j, so its
+    // stage-2 twiddles live in registers for the whole launch
+    constexpr bool TW_REG = LOG_N1 == LOG_N2;
+    WlTw<PA> treg;
+    if constexpr (TW_REG) {
+        const int u = tid % PA::GROUP;
+        treg.load(TWA, (u & 7) | ((u >> 4) << 3));
+    }
     int bb = 0;
     uint32_t par = 0;
     char *const Pc = reinterpret_cast<char *>(P);
@@ -409,7 +438,7 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const int group = tid / PS::GROUP, u = tid % PS::GROUP;
             const int c = 2 * group + ((u >> 3) & 1), j = (u & 7) | ((u >> 4) << 3);
             float2 v[32];
-            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA);
+            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA, TW_REG ? &treg : nullptr);
             // times w_n^{j2 k1}, k1 = j + P m: w_n^{j2 j} w_n^{j2 P m} (scale folded in), into the ring
             const float2 *Fb = F + bb * PS::FT;
             const float2 f1 = Fb[((c >> 1) * PS::P + j) * 2 + (c & 1)];
@@ -442,7 +471,8 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const int group = tid / PS::GROUP, u = tid % PS::GROUP;
             const int c = 2 * group + ((u >> 3) & 1), j = (u & 7) | ((u >> 4) << 3);
             float2 v[32];
-            wl_line<PS, S>(v, Pc, tb, c, j, group, TWB);
+            if constexpr (TW_REG) wl_line<PS, S>(v, Pc, tb, c, j, group, TWB, reinterpret_cast<const WlTw<PS> *>(&treg));
+            else wl_line<PS, S>(v, Pc, tb, c, j, group, TWB);
             const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
             const uint32_t rb = tb + (uint32_t)((c / PS::PW) * PS::PANEL_BYTES) + (uint32_t)(PS::ROWB * j) +
                                 (uint32_t)(16 * (ch ^ ((j7 >> PS::SWZ_S) & PS::SWZ_M)) + 8 * h);

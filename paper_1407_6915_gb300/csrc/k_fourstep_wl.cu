@@ -10,14 +10,15 @@ namespace {
 // 8192-point tiles, three buffers, one CTA per SM (eight compute warps of
 // 32 points per lane, a loader warp and a retirer warp).  Measured on GB300:
 // two buffers were 5-9 % slower.
-constexpr int kWlNb = 3;
+// (4096-point tiles at two CTAs per SM measured no faster at 2^16 and
+// 4-27 % slower at 2^17..2^20.)
+constexpr int kWlLogE = 13, kWlNb = 3, kWlMinB = 1;
 
-template <int LOG_N1, int LOG_N2, int S, int LOG_E>
+template <int LOG_N1, int LOG_N2, int S>
 cudaError_t wl_t(const FourStepWlArgs &a, cudaStream_t st)
 {
-    constexpr int MINB = LOG_E == 13 ? 1 : 2;
-    using Sh = FourStepWlShape<LOG_N1, LOG_N2, LOG_E, kWlNb, MINB>;
-    auto k = k_fourstep_wl<LOG_N1, LOG_N2, LOG_E, kWlNb, MINB, S>;
+    using Sh = FourStepWlShape<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB>;
+    auto k = k_fourstep_wl<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB, S>;
     // per device: the occupancy of this instantiation (the grid is the
     // resident CTAs of the GPU the launch goes to)
     static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
@@ -40,30 +41,30 @@ cudaError_t wl_t(const FourStepWlArgs &a, cudaStream_t st)
 }
 
 template <int LOG_N1, int LOG_N2>
-cudaError_t wl_s(int sign, int log_e, const FourStepWlArgs &a, cudaStream_t st)
+cudaError_t wl_s(int sign, const FourStepWlArgs &a, cudaStream_t st)
 {
-    if (log_e == 12) return sign < 0 ? wl_t<LOG_N1, LOG_N2, -1, 12>(a, st) : wl_t<LOG_N1, LOG_N2, 1, 12>(a, st);
-    return sign < 0 ? wl_t<LOG_N1, LOG_N2, -1, 13>(a, st) : wl_t<LOG_N1, LOG_N2, 1, 13>(a, st);
+    return sign < 0 ? wl_t<LOG_N1, LOG_N2, -1>(a, st) : wl_t<LOG_N1, LOG_N2, 1>(a, st);
 }
 
 }  // namespace
 
-bool fourstep_wl_shape(int log_n, int log_e, int *log_n1, int *log_n2)
+bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e)
 {
-    if (log_n < 16 || log_n > 20 || (log_e != 12 && log_e != 13)) return false;
+    if (log_n < 16 || log_n > 20) return false;
     *log_n1 = (log_n + 1) / 2;
     *log_n2 = log_n / 2;
+    *log_e = kWlLogE;
     return true;
 }
 
-cudaError_t launch_fourstep_wl(int log_n, int log_e, int sign, const FourStepWlArgs &a, cudaStream_t st)
+cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st)
 {
     switch (log_n) {
-        case 16: return wl_s<8, 8>(sign, log_e, a, st);
-        case 17: return wl_s<9, 8>(sign, log_e, a, st);
-        case 18: return wl_s<9, 9>(sign, log_e, a, st);
-        case 19: return wl_s<10, 9>(sign, log_e, a, st);
-        case 20: return wl_s<10, 10>(sign, log_e, a, st);
+        case 16: return wl_s<8, 8>(sign, a, st);
+        case 17: return wl_s<9, 8>(sign, a, st);
+        case 18: return wl_s<9, 9>(sign, a, st);
+        case 19: return wl_s<10, 9>(sign, a, st);
+        case 20: return wl_s<10, 10>(sign, a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -52,11 +52,9 @@ cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t s
 // output): lines of 256..1024 points with 32 points per lane, a queue of
 // column and row tiles, loader and retirer warps, swizzled TMA tiles.
 struct FourStepWlArgs;
-// Tiles of 2^log_e points: 13 (one CTA per SM) or 12 (two CTAs per SM).
-cudaError_t launch_fourstep_wl(int log_n, int log_e, int sign, const FourStepWlArgs &a, cudaStream_t st);
-// Factorisation n = N1 x N2 of the lane-line kernel (false: not built for
-// this length and tile size).
-bool fourstep_wl_shape(int log_n, int log_e, int *log_n1, int *log_n2);
+cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st);
+// Factorisation n = N1 x N2 and log2 of the tile size of the lane-line kernel.
+bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e);
 // Real-signal segments (k_real.cu): the pass between a length-n real DFT and
 // the length-m = n/2 complex DFT.  post: complex FFT output [nseg][m] -> the
 // n/2 + 1 bins [nseg][m + 1] (complex64, or float32 |X|^2 with power); pre:

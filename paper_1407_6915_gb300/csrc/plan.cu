@@ -190,10 +190,8 @@ int env_int(const char *name, int dflt, int lo, int hi)
 // column passes are tuning knobs read at plan creation.
 int build_fourstep_wl(fftseg_plan p)
 {
-    int l1, l2;
-    const int le = env_int("FFTSEG_WL_TILE_LOG2", 13, 12, 13);
-    if (!fourstep_wl_shape(p->log_n, le, &l1, &l2)) return set_error(FFTSEG_E_UNSUPPORTED, "lane-line shape");
-    p->wl_log_e = le;
+    int l1, l2, le;
+    if (!fourstep_wl_shape(p->log_n, &l1, &l2, &le)) return set_error(FFTSEG_E_UNSUPPORTED, "lane-line shape");
     p->path = PATH_FOURSTEP;
     p->log_n1 = l1;
     p->log_n2 = l2;
@@ -798,6 +796,8 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                                             (int)(pwb * 8));
                 if (rc != FFTSEG_OK) return rc;
                 const int64_t nc = (nseg + cs - 1) / cs;
+                if (nc * cs * ((n2 / wa) + (n1 / wb)) >= (int64_t(1) << 31))
+                    return set_error(FFTSEG_E_INVALID, "exec: too many tiles for one launch of the lane-line kernel");
                 a.ring = p->ring;
                 a.twA = p->twA;
                 a.twB = p->twB ? p->twB : p->twA;
@@ -812,7 +812,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 a.stall = (p->flags & FFTSEG_FLAG_TEST_STALL) ? 1 : 0;
                 e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
-                e = launch_fourstep_wl(p->log_n, p->wl_log_e, sign, a, st);
+                e = launch_fourstep_wl(p->log_n, sign, a, st);
                 if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
                 count_launches(1);
                 return FFTSEG_OK;

@@ -53,7 +53,6 @@ struct fftseg_plan_s {
     float2 *w4 = nullptr, *w4hi = nullptr;
     float2 *w4t = nullptr;  // the warp-line and lane-line kernels' factors, per column tile
     int wl_la = 0;          // lane-line kernel: chunks of lookahead of column over row passes
-    int wl_log_e = 13;      // lane-line kernel: log2 of the points per tile
     int w4_log_k = 0;
     int log_wa = 0, log_wb = 0;
     // real-signal plans (FFTSEG_FLAG_REAL): a complex plan of n/2 points
