@@ -316,24 +316,32 @@ def stream_bench(link, h_signal=None):
     out = {"n": n, "segments": nseg, "chunk_segments": chunk, "input_bytes": total,
            "generator": {"what": "tones + noise, seed 2, into pinned memory", "bytes": pool_segs * n * 8,
                          "s": round(gen_s, 3), "gbs": round(pool_segs * n * 8 / gen_s / 1e9, 3), "threads": cores}}
-    # full size, host-resident source
-    src = siggen.pool_source(pool.data_ptr(), pool_segs * n * 8, total, nthreads=min(cores, 16))
+    # full size, host-resident source lent in place (fftseg_stream_view): each
+    # chunk goes to the GPU straight from the pool
     snk = siggen.sink(None)  # counts the bytes, keeps nothing
-    rc, committed = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(src), siggen.write_fn_ptr(),
-                                ctypes.addressof(snk), 1 << 32, 0, chunk)  # warm-up: 4 GiB
-    t0 = time.perf_counter()
-    rc, committed = plan.stream(siggen.read_fn_ptr(), ctypes.addressof(src), siggen.write_fn_ptr(),
-                                ctypes.addressof(snk), total, 0, chunk)
-    wall = time.perf_counter() - t0
-    ph = plan.stream_phases()
-    h2d_gbs, d2h_gbs = total / wall / 1e9, total / 2 / wall / 1e9
-    out.update({"source": "2 GiB pinned pool of the seed-2 signal, read cyclically (%d copy threads)" % src.nthreads,
-                "status": rc, "committed_bytes": int(committed), "wall_s": round(wall, 3),
+
+    def full_run(lend):
+        src = siggen.pool_source(pool.data_ptr(), pool_segs * n * 8, total, nthreads=min(cores, 16))
+        go = plan.stream_view if lend else plan.stream
+        fn = siggen.view_fn_ptr() if lend else siggen.read_fn_ptr()
+        go(fn, ctypes.addressof(src), siggen.write_fn_ptr(), ctypes.addressof(snk), 1 << 32, 0, chunk)  # warm-up
+        t0 = time.perf_counter()
+        rc, committed = go(fn, ctypes.addressof(src), siggen.write_fn_ptr(), ctypes.addressof(snk), total, 0, chunk)
+        wall = time.perf_counter() - t0
+        ph = plan.stream_phases()
+        h2d_gbs, d2h_gbs = total / wall / 1e9, total / 2 / wall / 1e9
+        return {"status": rc, "committed_bytes": int(committed), "wall_s": round(wall, 3),
                 "gflops": round(flops_per_transform(n, nseg) / wall / 1e9, 1),
                 "h2d_gbs": round(h2d_gbs, 2), "d2h_gbs": round(d2h_gbs, 2),
                 "link_frac": round(max(h2d_gbs / link["h2d"], d2h_gbs / link["d2h"]), 4),
                 "phases_ms": {k: round(v, 1) for k, v in ph.items()},
-                "bound": "reader" if ph["read_ms"] > 0.8 * ph["wall_ms"] else "pipeline"})
+                "bound": "reader" if ph["read_ms"] > 0.8 * ph["wall_ms"] else "pipeline"}
+
+    out["source"] = "2 GiB pinned pool of the seed-2 signal, read cyclically"
+    out.update(full_run(True))
+    out["call"] = "fftseg_stream_view (the pool lent in place)"
+    out["copying_reader"] = dict(full_run(False), call="fftseg_stream, the reader copying from the pool "
+                                 "(%d threads)" % min(cores, 16))
     # a generator-fed sample (2 GiB)
     gseg = 256
     gsrc = siggen.source(siggen.KIND_TONES, 2, gseg * n * 8)

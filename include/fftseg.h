@@ -207,6 +207,26 @@ int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn 
                   int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
                   int64_t *committed_offset);
 
+/* A source that lends the signal's bytes instead of copying them: returns the
+ * host address of the bytes [byte_offset, byte_offset + bytes) -- all of them,
+ * or fewer only where the signal ends (the count in *got) -- or NULL on
+ * failure.  The memory must stay valid and unchanged until the stream call
+ * returns: a signal already in host memory (a pinned buffer, a mapped file).
+ * Pinned memory goes to the GPU at the host link's rate; pageable memory
+ * through the driver's own staging, more slowly. */
+typedef const void *(*fftseg_view_fn)(void *ctx, int64_t byte_offset, int64_t bytes, int64_t *got);
+
+/* fftseg_stream with a lending source (fftseg_view_fn) in place of the reader:
+ * each chunk is copied to the GPU straight from the lent memory, with no copy
+ * into the chunker's pinned buffers (Sec. III's one copy per block).  The same
+ * segmenting, positional output, partial-tail rules and resume offset as
+ * fftseg_stream; the writer is called the same way.  Segment plans only (frame
+ * plans: FFTSEG_E_UNSUPPORTED).  A NULL from the source ends the call with
+ * FFTSEG_E_IO at that offset. */
+int fftseg_stream_view(fftseg_plan p, fftseg_view_fn view, void *vctx, fftseg_write_fn wr, void *wctx,
+                       int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
+                       int64_t *committed_offset);
+
 /*
  * File-backed streaming: the paper's pipeline end to end on one GPU (Sec. III,
  * a signal file cut into segments, each transformed, the results written in

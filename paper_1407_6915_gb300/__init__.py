@@ -46,6 +46,8 @@ STATUS_NAMES = {0: "OK", -1: "E_INVALID", -2: "E_NOMEM", -3: "E_CUDA", -4: "E_IO
                 -6: "E_TIMEOUT", -7: "E_UNSUPPORTED"}
 
 READ_FN = ctypes.CFUNCTYPE(ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64)
+VIEW_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                           ctypes.POINTER(ctypes.c_int64))
 WRITE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64)
 
 
@@ -79,6 +81,9 @@ _SIGS = {
     "fftseg_stream": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                      ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                      ctypes.POINTER(ctypes.c_int64)]),
+    "fftseg_stream_view": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.POINTER(ctypes.c_int64)]),
     "fftseg_stream_phases": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     "fftseg_stream_file": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_int64,
                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_uint,
@@ -263,6 +268,37 @@ class Plan:
                                  ctypes.byref(committed))
         if rc not in (OK, E_IO, E_PARTIAL):
             check(rc, "fftseg_stream")
+        return rc, committed.value
+
+    def stream_view(self, view, vctx, writer, wctx, total_bytes, start_offset=0, chunk_segments=0):
+        """fftseg_stream_view: `view` lends the signal's host memory (a C
+        function pointer (int) with its context, or a Python callable
+        (ctx, offset, nbytes) -> (address, nbytes) or None).  Returns
+        (status, committed_offset) and does not raise on E_IO/E_PARTIAL."""
+        keep = []
+        if isinstance(view, int):
+            vfn = ctypes.c_void_p(view)
+        else:
+            def shim(ctx, off, nbytes, got):
+                r = view(ctx, off, nbytes)
+                if r is None:
+                    return None
+                got[0] = int(r[1])
+                return int(r[0])
+            cb = VIEW_FN(shim)
+            keep.append(cb)
+            vfn = ctypes.cast(cb, ctypes.c_void_p)
+        if isinstance(writer, int):
+            wfn = ctypes.c_void_p(writer)
+        else:
+            wcb = WRITE_FN(writer)
+            keep.append(wcb)
+            wfn = ctypes.cast(wcb, ctypes.c_void_p)
+        committed = ctypes.c_int64(0)
+        rc = lib().fftseg_stream_view(self._h, vfn, vctx, wfn, wctx, int(total_bytes), int(start_offset),
+                                      int(chunk_segments), ctypes.byref(committed))
+        if rc not in (OK, E_IO, E_PARTIAL):
+            check(rc, "fftseg_stream_view")
         return rc, committed.value
 
     def stream_file(self, in_path, out_path, start_offset=0, chunk_segments=0, direct=True, end_offset=0,

@@ -111,6 +111,19 @@ void segment_bytes(const fftseg_plan_s *p, int64_t *in, int64_t *out)
 
 using namespace fftseg;
 
+namespace fftseg {
+namespace {
+
+// The segment-plan chunker, fed either by a reader that copies each chunk
+// into the ring's pinned buffer (rd) or by a source that lends the chunk's
+// bytes in place (view): then the copy to the GPU reads the source directly.
+int stream_segments(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_view_fn view, void *vctx,
+                    fftseg_write_fn wr, void *wctx, int64_t total_bytes, int64_t start_offset,
+                    int64_t chunk_segments, int64_t *committed_offset);
+
+}  // namespace
+}  // namespace fftseg
+
 extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_write_fn wr, void *wctx,
                              int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
                              int64_t *committed_offset)
@@ -119,6 +132,29 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
     if (!p || !rd || !wr) return set_error(FFTSEG_E_INVALID, "stream: NULL plan or callback");
     if (p->path == PATH_FRAMES)
         return stream_frames(p, rd, rctx, wr, wctx, total_bytes, start_offset, chunk_segments, committed_offset);
+    return stream_segments(p, rd, rctx, nullptr, nullptr, wr, wctx, total_bytes, start_offset, chunk_segments,
+                           committed_offset);
+}
+
+extern "C" int fftseg_stream_view(fftseg_plan p, fftseg_view_fn view, void *vctx, fftseg_write_fn wr, void *wctx,
+                                  int64_t total_bytes, int64_t start_offset, int64_t chunk_segments,
+                                  int64_t *committed_offset)
+{
+    if (committed_offset) *committed_offset = start_offset;
+    if (!p || !view || !wr) return set_error(FFTSEG_E_INVALID, "stream_view: NULL plan or callback");
+    if (p->path == PATH_FRAMES)
+        return set_error(FFTSEG_E_UNSUPPORTED, "stream_view: frame plans stream through fftseg_stream");
+    return stream_segments(p, nullptr, nullptr, view, vctx, wr, wctx, total_bytes, start_offset, chunk_segments,
+                           committed_offset);
+}
+
+namespace fftseg {
+namespace {
+
+int stream_segments(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftseg_view_fn view, void *vctx,
+                    fftseg_write_fn wr, void *wctx, int64_t total_bytes, int64_t start_offset,
+                    int64_t chunk_segments, int64_t *committed_offset)
+{
     int64_t seg_in = 0, seg_out = 0;
     segment_bytes(p, &seg_in, &seg_out);
     if (total_bytes < 0 || start_offset < 0 || start_offset > total_bytes || start_offset % seg_in)
@@ -177,7 +213,15 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
         int64_t want = total_bytes - offset;
         if (want > ring.in_bytes) want = ring.in_bytes;
         const double t0 = now_ms();
-        const int64_t got = rd(rctx, offset, ring.h_in[i], want);
+        int64_t got = -1;
+        const void *src = ring.h_in[i];  // where this chunk's bytes are
+        if (view) {
+            const void *lent = view(vctx, offset, want, &got);
+            if (!lent) got = -1;
+            src = lent;
+        } else {
+            got = rd(rctx, offset, ring.h_in[i], want);
+        }
         t_read += now_ms() - t0;
         if (got < 0 || got > want) {
             status = set_error(FFTSEG_E_IO, "stream: reader failed at input offset %lld", (long long)offset);
@@ -188,6 +232,10 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
         const int64_t tail = got - segs * seg_in;
         if (tail) {
             if (zero_pad) {
+                if (src != ring.h_in[i]) {  // a lent tail is padded in the ring's own buffer
+                    memcpy(ring.h_in[i], src, (size_t)got);
+                    src = ring.h_in[i];
+                }
                 memset(static_cast<char *>(ring.h_in[i]) + got, 0, (size_t)(seg_in - tail));
                 ++segs;
             } else {
@@ -200,8 +248,8 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
             cudaError_t e;
             const int64_t bytes = segs * seg_in;
             if ((e = cudaEventRecord(ring.e0[i], ring.s_h2d)) != cudaSuccess ||
-                (e = cudaMemcpyAsync(ring.d_in[i], ring.h_in[i], (size_t)bytes, cudaMemcpyHostToDevice,
-                                     ring.s_h2d)) != cudaSuccess ||
+                (e = cudaMemcpyAsync(ring.d_in[i], src, (size_t)bytes, cudaMemcpyHostToDevice, ring.s_h2d)) !=
+                    cudaSuccess ||
                 (e = cudaEventRecord(ring.e_h2d[i], ring.s_h2d)) != cudaSuccess ||
                 (e = cudaStreamWaitEvent(ring.s_comp, ring.e_h2d[i], 0)) != cudaSuccess) {
                 status = cuda_error(e, "stream: copy-in");
@@ -256,6 +304,9 @@ extern "C" int fftseg_stream(fftseg_plan p, fftseg_read_fn rd, void *rctx, fftse
     if (committed_offset) *committed_offset = committed;
     return status;
 }
+
+}  // namespace
+}  // namespace fftseg
 
 namespace fftseg {
 namespace {

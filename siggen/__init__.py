@@ -66,6 +66,8 @@ def lib():
                                          ctypes.c_void_p, ctypes.c_void_p]
         L.siggen_read.restype = ctypes.c_int64
         L.siggen_read.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
+        L.siggen_view.restype = ctypes.c_void_p
+        L.siggen_view.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         L.siggen_write.restype = ctypes.c_int
         L.siggen_write.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
         _lib = L
@@ -148,6 +150,11 @@ def sink(buf=None, fail_at_call: int = -1) -> Sink:
                     bytes_written=0, last_offset=-1)
     return Sink(base=buf.ctypes.data, capacity=buf.nbytes, fail_at_call=fail_at_call, pad=0,
                 calls=0, bytes_written=0, last_offset=-1)
+
+
+def view_fn_ptr() -> int:
+    """siggen_view: the lending source of fftseg_stream_view over a pool source."""
+    return ctypes.cast(lib().siggen_view, ctypes.c_void_p).value
 
 
 def read_fn_ptr() -> int:

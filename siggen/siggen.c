@@ -340,6 +340,27 @@ int64_t siggen_read(void *ctx, int64_t byte_offset, void *dst, int64_t bytes)
 }
 
 /*
+ * Lending source for fftseg_stream_view (pool sources only): the address of
+ * the pool's bytes for [byte_offset, byte_offset + bytes), bounded by
+ * total_bytes (*got), or NULL if the range wraps past the pool's end (make the
+ * pool a multiple of the chunk bytes) or on an injected failure.
+ */
+const void *siggen_view(void *ctx, int64_t byte_offset, int64_t bytes, int64_t *got)
+{
+    siggen_source *src = (siggen_source *)ctx;
+    if (!src || !got || src->kind != 2 || !src->pool || src->pool_bytes <= 0 || byte_offset < 0 || bytes < 0)
+        return NULL;
+    const int64_t call = src->calls++;
+    if (src->fail_at_call >= 0 && call == src->fail_at_call) return NULL;
+    if (bytes > src->total_bytes - byte_offset) bytes = src->total_bytes - byte_offset;
+    if (bytes < 0) bytes = 0;
+    const int64_t o = byte_offset % src->pool_bytes;
+    if (o + bytes > src->pool_bytes) return NULL;
+    *got = bytes;
+    return src->pool + o;
+}
+
+/*
  * Writer context: a host buffer that receives each output block at its byte
  * offset (positional order, Sec. III "getmerge" of files named by position).
  * base may be NULL: then the writer only counts bytes (a discarding sink).

@@ -162,3 +162,86 @@ def test_stream_argument_errors():
         plan.stream(rd_ptr(), ctypes.addressof(src), wr_ptr(), ctypes.addressof(snk), 8192 * 4, 100, 4)
     with pytest.raises(fs.FFTSegError):
         plan.stream(rd_ptr(), ctypes.addressof(src), wr_ptr(), ctypes.addressof(snk), 8192 * 4, 0, 5)
+
+
+# ------------------------------------------------- lending sources (view)
+
+@pytest.mark.parametrize("log_n,chunk,out_kind", [(10, 64, fs.OUT_COMPLEX), (16, 8, fs.OUT_POWER),
+                                                  (17, 4, fs.OUT_COMPLEX)])
+def test_stream_view_equals_copying_reader(log_n, chunk, out_kind):
+    # a pinned pool lent in place (fftseg_stream_view) gives the same bits as
+    # the copying reader over the same bytes, and matches the oracle
+    n = 1 << log_n
+    nseg = 5 * chunk + 3  # a partial last chunk
+    total = nseg * n * 8
+    pool = torch.empty(nseg * n, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_TONES, 21, 0, nseg * n, pool.data_ptr())
+    plan = fs.Plan(n, chunk, fs.FORWARD, out_kind=out_kind)
+    seg_out = n * (4 if out_kind == fs.OUT_POWER else 8)
+    a = np.zeros(nseg * seg_out, dtype=np.uint8)
+    b = np.zeros(nseg * seg_out, dtype=np.uint8)
+    # (every ctypes context the C side holds a pointer to stays referenced)
+    src, snk_a = siggen.pool_source(pool.data_ptr(), total, total), siggen.sink(a)
+    rc, committed = plan.stream_view(siggen.view_fn_ptr(), ctypes.addressof(src), wr_ptr(),
+                                     ctypes.addressof(snk_a), total, 0, chunk)
+    assert rc == fs.OK and committed == total
+    src2, snk_b = siggen.pool_source(pool.data_ptr(), total, total), siggen.sink(b)
+    rc, committed = plan.stream(rd_ptr(), ctypes.addressof(src2), wr_ptr(), ctypes.addressof(snk_b),
+                                total, 0, chunk)
+    assert rc == fs.OK and committed == total
+    np.testing.assert_array_equal(a, b)
+    x = pool.numpy().reshape(nseg, n)
+    if out_kind == fs.OUT_POWER:
+        assert rel_l2(a.view(np.float32).reshape(nseg, n), oracle.power(x)) <= tol_power(n)
+    else:
+        assert rel_l2(a.view(np.complex64).reshape(nseg, n), oracle.fft(x)) <= tol_fp32(n)
+
+
+def test_stream_view_failure_resume_and_tail():
+    n, chunk, nseg = 1 << 12, 16, 70
+    total = nseg * n * 8
+    pool = torch.empty(nseg * n, dtype=torch.complex64, pin_memory=True)
+    siggen.fill_pointer(siggen.KIND_UNIFORM, 22, 0, nseg * n, pool.data_ptr())
+    plan = fs.Plan(n, chunk, fs.FORWARD)
+    ref = plan.exec(pool.cuda().view(nseg, n)[:chunk], nseg=chunk)  # the first chunk, resident
+    out = np.zeros(nseg * n * 8, dtype=np.uint8)
+    # the source fails on its third call: two chunks are complete, E_IO, and
+    # the committed offset is where a later call resumes
+    src, snk = siggen.pool_source(pool.data_ptr(), total, total, fail_at_call=2), siggen.sink(out)
+    rc, committed = plan.stream_view(siggen.view_fn_ptr(), ctypes.addressof(src), wr_ptr(),
+                                     ctypes.addressof(snk), total, 0, chunk)
+    assert rc == fs.E_IO and committed == 2 * chunk * n * 8
+    src, snk = siggen.pool_source(pool.data_ptr(), total, total), siggen.sink(out)
+    rc, committed = plan.stream_view(siggen.view_fn_ptr(), ctypes.addressof(src), wr_ptr(),
+                                     ctypes.addressof(snk), total, committed, chunk)
+    assert rc == fs.OK and committed == total
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.view(np.complex64)[:chunk * n], ref.cpu().numpy().ravel())
+    full = fs.Plan(n, nseg, fs.FORWARD).exec(pool.cuda().view(nseg, n)).cpu().numpy().ravel()
+    np.testing.assert_array_equal(out.view(np.complex64), full)
+    # a signal that ends inside a segment: E_PARTIAL, or zero-padded with the flag
+    short = total - 3 * 8
+    scratch = np.zeros_like(out)
+    src, snk = siggen.pool_source(pool.data_ptr(), total, short), siggen.sink(scratch)
+    rc, committed = plan.stream_view(siggen.view_fn_ptr(), ctypes.addressof(src), wr_ptr(),
+                                     ctypes.addressof(snk), short, 0, chunk)
+    assert rc == fs.E_PARTIAL and committed == (nseg - 1) * n * 8
+    padded = fs.Plan(n, chunk, fs.FORWARD, flags=fs.FLAG_ZERO_PAD)
+    out2 = np.zeros_like(out)
+    src, snk = siggen.pool_source(pool.data_ptr(), total, short), siggen.sink(out2)
+    rc, committed = padded.stream_view(siggen.view_fn_ptr(), ctypes.addressof(src), wr_ptr(),
+                                       ctypes.addressof(snk), short, 0, chunk)
+    assert rc == fs.OK
+    last = pool.numpy()[(nseg - 1) * n:].copy()
+    last[-3:] = 0
+    want = oracle.fft(last.reshape(1, n))
+    assert rel_l2(out2.view(np.complex64)[(nseg - 1) * n:].reshape(1, n), want) <= tol_fp32(n)
+    # frame plans stream through the copying reader only
+    fp = fs.FramePlan(n, n // 2, 4)
+    assert lib_status(fp) == fs.E_UNSUPPORTED
+
+
+def lib_status(plan):
+    committed = ctypes.c_int64(0)
+    return fs.lib().fftseg_stream_view(plan._h, ctypes.c_void_p(siggen.view_fn_ptr()), None,
+                                       ctypes.c_void_p(wr_ptr()), None, 1 << 20, 0, 0, ctypes.byref(committed))
