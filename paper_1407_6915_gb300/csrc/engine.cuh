@@ -450,6 +450,17 @@ FDEV void tma_load_3d(void *dst, const CUtensorMap *tmap, int x, int y, int z, u
         : "memory");
 }
 
+// Tiled 2-D TMA load of one box of `tmap` at (x, y) into shared memory with
+// an L2 cache policy, completed on *bar (x * element size a multiple of 16).
+FDEV void tma_load_2d_hint(void *dst, const CUtensorMap *tmap, int x, int y, uint64_t *bar, uint64_t policy)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+        : "memory");
+}
+
 // Tiled 4-D TMA load of one box of `tmap` at element coordinates (x, y, z, w)
 // into shared memory, completed on *bar (x * element size a multiple of 16).
 FDEV void tma_load_4d(void *dst, const CUtensorMap *tmap, int x, int y, int z, int w, uint64_t *bar)
@@ -459,6 +470,15 @@ FDEV void tma_load_4d(void *dst, const CUtensorMap *tmap, int x, int y, int z, i
         " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
         "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
         : "memory");
+}
+
+// L2 cache policy that leaves a line's eviction priority as it is (for data
+// that is read twice, such as the overlap of consecutive frames).
+FDEV uint64_t policy_evict_unchanged()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_unchanged.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 // L2 cache policy: lines fetched or written under it are evicted first (for

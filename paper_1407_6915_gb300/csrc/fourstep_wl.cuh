@@ -65,6 +65,15 @@ struct FourStepWlArgs {
     int cs;              // segments per chunk
     int nr;              // ring chunks (>= la + 2)
     int la;              // column passes run this many chunks ahead of row passes (>= 1)
+    // overlapping frames (a frame plan whose hop is a multiple of N2): frame s
+    // starts frame_rows rows of N2 samples after frame s - 1, and tmA is then
+    // the 2-D map of the signal's rows, box [PW_A][256]; 0 for segments
+    int frame_rows;
+    // periodic Hann window on the frames, w[j1 N2 + j2] = (1 - cos(2 pi (j1/N1 + j2/n))) / 2,
+    // from win_row[j1] = (cos, sin)(2 pi j1 / N1) and win_col[j2] = (cos, sin)(2 pi j2 / n);
+    // null: no window
+    const float2 *win_row;
+    const float2 *win_col;
     int stall;           // test only: segment 0's row tiles wait for one column tile more than
                          // exists, with a short spin limit, so that the bounded wait runs out
 };
@@ -147,7 +156,7 @@ struct WlTw {
 // tw: stage-2 twiddles in shared memory, or (treg) the lane's own in registers.
 template <class PS, int S>
 FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int group, const float2 *tw,
-                  const WlTw<PS> *treg = nullptr)
+                  const WlTw<PS> *treg = nullptr, const float2 *wrow = nullptr, float2 wcol = float2{})
 {
     constexpr int P = PS::P, Q = PS::Q, ROWB = PS::ROWB;
     const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
@@ -160,6 +169,14 @@ FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int grou
     auto at = [&](uint32_t off) -> float2 & { return *reinterpret_cast<float2 *>(Pc + off); };
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = at(rb + ROWB * P * r);
+    if (wrow) {  // the frame's window on rows j + P r of this column
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const float2 rr = __ldg(wrow + j + P * r);
+            const float wv = 0.5f - 0.5f * (rr.x * wcol.x - rr.y * wcol.y);
+            v[r] = make_float2(v[r].x * wv, v[r].y * wv);
+        }
+    }
     dft32<S>(v);
     wl_group_sync<PS::GROUP>(group);  // every lane of the line has read its rows
 #pragma unroll
@@ -333,7 +350,10 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             w = t3 - (t3 / TB) * TB;
         };
         int64_t a_seen = -1, b_seen = -1;  // highest segment whose column / row tiles were seen complete
-        const uint64_t stream_policy = policy_evict_first();  // the input is read once
+        // the input is read once (evicted first), except where consecutive
+        // frames overlap: then the overlap is read again by the next frame
+        const bool overlap = a.frame_rows > 0 && (int64_t)a.frame_rows * Sh::N2 < Sh::N;
+        const uint64_t stream_policy = overlap ? policy_evict_unchanged() : policy_evict_first();
         int t = 0;
         if (lane == 0) t = atomicAdd(a.ctr, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
@@ -381,10 +401,15 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
 #pragma unroll
                             for (int p = 0; p < PA::NPANEL; ++p)
 #pragma unroll
-                                for (int q = 0; q < PA::NBOXY; ++q)
-                                    tma_load_3d_hint(dst + p * PA::PANEL_BYTES + q * 256 * PA::ROWB, &a.tmA,
-                                                     tile * PA::W + p * PA::PW, q * 256, (int)s, &full[b],
-                                                     stream_policy);
+                                for (int q = 0; q < PA::NBOXY; ++q) {
+                                    char *box = dst + p * PA::PANEL_BYTES + q * 256 * PA::ROWB;
+                                    const int x = tile * PA::W + p * PA::PW;
+                                    if (a.frame_rows)  // rows of the signal from the frame's start
+                                        tma_load_2d_hint(box, &a.tmA, x, (int)s * a.frame_rows + q * 256, &full[b],
+                                                         stream_policy);
+                                    else
+                                        tma_load_3d_hint(box, &a.tmA, x, q * 256, (int)s, &full[b], stream_policy);
+                                }
                             tma_load_1d(F + b * PA::FT, a.w4t + (int64_t)tile * PA::FT, Sh::F_BYTES, &full[b]);
                         } else {
                             mbar_expect_tx(&full[b], Sh::TILE_BYTES);
@@ -438,7 +463,8 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const int group = tid / PS::GROUP, u = tid % PS::GROUP;
             const int c = 2 * group + ((u >> 3) & 1), j = (u & 7) | ((u >> 4) << 3);
             float2 v[32];
-            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA, TW_REG ? &treg : nullptr);
+            const float2 wcol = a.win_row ? __ldg(a.win_col + ct * PS::W + c) : float2{};
+            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA, TW_REG ? &treg : nullptr, a.win_row, wcol);
             // times w_n^{j2 k1}, k1 = j + P m: w_n^{j2 j} w_n^{j2 P m} (scale folded in), into the ring
             const float2 *Fb = F + bb * PS::FT;
             const float2 f1 = Fb[((c >> 1) * PS::P + j) * 2 + (c & 1)];

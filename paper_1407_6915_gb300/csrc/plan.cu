@@ -161,6 +161,8 @@ void free_plan(fftseg_plan p)
     cudaFree(p->rtw);
     cudaFree(p->rwork);
     cudaFree(p->fwin);
+    cudaFree(p->win_row);
+    cudaFree(p->win_col);
     if (p->host_stage && p->host_stage_free) p->host_stage_free(p->host_stage);
     cudaFree(p->twA);
     cudaFree(p->twB);
@@ -411,7 +413,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_REAL:
         case PATH_FRAMES: {
             if (p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) return 1;
-            if (frames_fused(p)) return 1;
+            if (frames_fused(p) || p->frames_wl) return 1;
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
                 k += 1 + launches_per_exec(p->inner, nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk);
@@ -471,6 +473,71 @@ int encode_tmap(CUtensorMap *m, const void *base, int rank, const int64_t *dims_
                         CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return set_error(FFTSEG_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return FFTSEG_OK;
+}
+
+// The lane-line four-step kernel over nseg segments, or (fr) over the nseg
+// frames of a frame plan whose hop is a multiple of N2 (the frames' column
+// tiles come straight from the signal, windowed as they are read).
+struct WlFrames {
+    int64_t hop;
+    const float2 *win_row, *win_col;  // null: rectangular window
+};
+
+int exec_fourstep_wl(fftseg_plan p, const void *in, void *d_out, int64_t nseg, cudaStream_t st, const WlFrames *fr)
+{
+    const int64_t n = p->n;
+    const int cs = (int)(nseg < p->ring_cs ? nseg : p->ring_cs);
+    FourStepWlArgs a{};
+    const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
+    const int64_t wa = int64_t(1) << p->log_wa, wb = int64_t(1) << p->log_wb;
+    const int64_t pwa = wa < 16 ? wa : 16, pwb = wb < 16 ? wb : 16;
+    const int64_t slabs = (int64_t)p->ring_nr * cs;
+    int rc;
+    if (fr) {
+        // the signal as rows of N2 samples: frame s starts at row s * hop / N2
+        const int64_t rows = ((nseg - 1) * fr->hop + n) / n2;
+        if (rows >= (int64_t(1) << 31)) return set_error(FFTSEG_E_INVALID, "exec: signal too long for one launch");
+        const int64_t dims[2] = {n2, rows};
+        const int64_t strides[1] = {n2 * 8};
+        const uint32_t box[2] = {(uint32_t)pwa, 256};
+        rc = encode_tmap(&a.tmA, in, 2, dims, strides, box, 8, (int)(pwa * 8));
+        a.frame_rows = (int)(fr->hop / n2);
+        a.win_row = fr->win_row;
+        a.win_col = fr->win_col;
+    } else {
+        rc = encode_tmap_3d_swz(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, (uint32_t)pwa, 256, 8, (int)(pwa * 8));
+    }
+    if (rc == FFTSEG_OK) {
+        // ring blocks [slab][k1 / wb][j2][k1 mod wb]
+        const int64_t dims[4] = {wb, n2, n1 / wb, slabs};
+        const int64_t strides[3] = {wb * 8, n2 * wb * 8, n * 8};
+        const uint32_t box[4] = {(uint32_t)pwb, 256, 1, 1};
+        rc = encode_tmap(&a.tmB, p->ring, 4, dims, strides, box, 8, (int)(pwb * 8));
+    }
+    if (rc == FFTSEG_OK)
+        rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8, (int)(pwb * 8));
+    if (rc != FFTSEG_OK) return rc;
+    const int64_t nc = (nseg + cs - 1) / cs;
+    if (nc * cs * ((n2 / wa) + (n1 / wb)) >= (int64_t(1) << 31))
+        return set_error(FFTSEG_E_INVALID, "exec: too many tiles for one launch of the lane-line kernel");
+    a.ring = p->ring;
+    a.twA = p->twA;
+    a.twB = p->twB ? p->twB : p->twA;
+    a.w4t = p->w4t;
+    a.ctr = p->ctr;
+    a.err = p->d_err;
+    a.nseg = nseg;
+    a.nchunks = (int)nc;
+    a.cs = cs;
+    a.nr = p->ring_nr;
+    a.la = p->wl_la;
+    a.stall = (p->flags & FFTSEG_FLAG_TEST_STALL) ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+    e = launch_fourstep_wl(p->log_n, p->direction, a, st);
+    if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
+    count_launches(1);
     return FFTSEG_OK;
 }
 
@@ -571,6 +638,11 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
         if (e != cudaSuccess) return cuda_error(e, "frames block kernel launch");
         count_launches(1);
         return FFTSEG_OK;
+    }
+    if (p->path == PATH_FRAMES && p->frames_wl) {
+        // one launch: the frames' column tiles straight from the signal
+        const WlFrames fr{p->hop, p->win_row, p->win_col};
+        return exec_fourstep_wl(p->inner, d_in, d_out, nseg, st, &fr);
     }
     if (p->path == PATH_FRAMES) {
         // chunks of rchunk frames: windowed frames into an L2-sized
@@ -775,48 +847,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
                 count_launches(1);
                 return FFTSEG_OK;
             }
-            if (uses_fourstep_wl(p)) {
-                // lane-local lines of 256..1024 points, a queue of tiles, TMA loads and stores
-                FourStepWlArgs a{};
-                const int64_t n1 = int64_t(1) << p->log_n1, n2 = int64_t(1) << p->log_n2;
-                const int64_t wa = int64_t(1) << p->log_wa, wb = int64_t(1) << p->log_wb;
-                const int64_t pwa = wa < 16 ? wa : 16, pwb = wb < 16 ? wb : 16;
-                const int64_t slabs = (int64_t)p->ring_nr * cs;
-                int rc = encode_tmap_3d_swz(&a.tmA, in, n2, n1, nseg, n2 * 8, n * 8, (uint32_t)pwa, 256, 8,
-                                            (int)(pwa * 8));
-                if (rc == FFTSEG_OK) {
-                    // ring blocks [slab][k1 / wb][j2][k1 mod wb]
-                    const int64_t dims[4] = {wb, n2, n1 / wb, slabs};
-                    const int64_t strides[3] = {wb * 8, n2 * wb * 8, n * 8};
-                    const uint32_t box[4] = {(uint32_t)pwb, 256, 1, 1};
-                    rc = encode_tmap(&a.tmB, p->ring, 4, dims, strides, box, 8, (int)(pwb * 8));
-                }
-                if (rc == FFTSEG_OK)
-                    rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8,
-                                            (int)(pwb * 8));
-                if (rc != FFTSEG_OK) return rc;
-                const int64_t nc = (nseg + cs - 1) / cs;
-                if (nc * cs * ((n2 / wa) + (n1 / wb)) >= (int64_t(1) << 31))
-                    return set_error(FFTSEG_E_INVALID, "exec: too many tiles for one launch of the lane-line kernel");
-                a.ring = p->ring;
-                a.twA = p->twA;
-                a.twB = p->twB ? p->twB : p->twA;
-                a.w4t = p->w4t;
-                a.ctr = p->ctr;
-                a.err = p->d_err;
-                a.nseg = nseg;
-                a.nchunks = (int)nc;
-                a.cs = cs;
-                a.nr = p->ring_nr;
-                a.la = p->wl_la;
-                a.stall = (p->flags & FFTSEG_FLAG_TEST_STALL) ? 1 : 0;
-                e = cudaMemsetAsync(p->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
-                if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
-                e = launch_fourstep_wl(p->log_n, sign, a, st);
-                if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
-                count_launches(1);
-                return FFTSEG_OK;
-            }
+            if (uses_fourstep_wl(p)) return exec_fourstep_wl(p, in, d_out, nseg, st, nullptr);
             if (uses_fourstep_hw(p)) {
                 // n = 256 x 256: warp-local lines, loader and retirer warps, TMA output stores
                 FourStepHwArgs a{};
@@ -963,8 +994,23 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
     if (cs < 1) cs = 1;
     if (cs > batch) cs = batch;
     p->rchunk = cs;
-    int rc = fftseg_plan_create(&p->inner, n, cs, FFTSEG_FORWARD, norm, FFTSEG_PREC_FP32, out_kind, flags);
-    if (rc == FFTSEG_OK && window == FFTSEG_WINDOW_HANN) {
+    // the inner plan takes the whole batch: the fused lane-line form runs it
+    // in one launch; the chunked form calls it a chunk at a time
+    int rc = fftseg_plan_create(&p->inner, n, batch, FFTSEG_FORWARD, norm, FFTSEG_PREC_FP32, out_kind, flags);
+    if (rc == FFTSEG_OK && uses_fourstep_wl(p->inner) && hop % (int64_t(1) << p->inner->log_n2) == 0) {
+        p->frames_wl = true;
+        if (window == FFTSEG_WINDOW_HANN) {
+            const int64_t n1 = int64_t(1) << p->inner->log_n1, n2 = int64_t(1) << p->inner->log_n2;
+            std::vector<float2> r((size_t)n1), c((size_t)n2);
+            host_roots(r.data(), n1, n1, 1);  // (cos, -sin)(2 pi j1 / N1)
+            host_roots(c.data(), n2, n, 1);   // (cos, -sin)(2 pi j2 / n)
+            for (auto &v : r) v.y = -v.y;
+            for (auto &v : c) v.y = -v.y;
+            rc = upload(&p->win_row, r);
+            if (rc == FFTSEG_OK) rc = upload(&p->win_col, c);
+        }
+    }
+    if (rc == FFTSEG_OK && window == FFTSEG_WINDOW_HANN && !p->frames_wl) {
         // periodic Hann window, w[j] = (1 - cos(2 pi j / n)) / 2, evaluated in double
         std::vector<float> h((size_t)n);
         const double two_pi = 6.283185307179586476925286766559;
@@ -974,8 +1020,9 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
         if (e != cudaSuccess) rc = cuda_error(e, "window table");
     }
     if (rc == FFTSEG_OK) {
-        // fused frames (n <= 4096) need no intermediate
-        e = frames_fused(p) ? cudaSuccess : cudaMalloc((void **)&p->rwork, (size_t)(cs * n) * sizeof(float2));
+        // fused frames (n <= 4096, or on the lane-line kernel) need no intermediate
+        e = (frames_fused(p) || p->frames_wl) ? cudaSuccess
+                                               : cudaMalloc((void **)&p->rwork, (size_t)(cs * n) * sizeof(float2));
         if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(frames intermediate)");

@@ -64,6 +64,12 @@ struct fftseg_plan_s {
     int64_t hop = 0;
     int window = 0;
     float *fwin = nullptr;  // the window, n values (null: rectangular)
+    // frame plans on the lane-line kernel (hop a multiple of N2, complex
+    // output): frames go straight from the signal into its column tiles, the
+    // Hann window from the factors win_row[j1] = (cos, sin)(2 pi j1 / N1),
+    // win_col[j2] = (cos, sin)(2 pi j2 / n)
+    bool frames_wl = false;
+    float2 *win_row = nullptr, *win_col = nullptr;
     // lengths that are not powers of two: inner (forward) and inner2 (inverse)
     // M-point plans, the chirp and B = FFT_M(conjugate chirp) / M; rwork holds
     // a chunk of M-point rows
