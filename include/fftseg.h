@@ -318,7 +318,10 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6]);
 
 /* Synchronise with the device and report whether any kernel of this plan
  * gave up a bounded wait since the last check (FFTSEG_E_TIMEOUT; the outputs
- * of that call are then not valid) -- FFTSEG_OK otherwise.  Clears the flag. */
+ * of that call are then not valid) -- FFTSEG_OK otherwise.  Clears the flag.
+ * In the self-checking build (libfftseg_debug.so, compiled with
+ * -DFFTSEG_DEBUG) a kernel that finds one of its indices outside its buffer
+ * skips that access and this call returns FFTSEG_E_INVALID. */
 int fftseg_plan_check(fftseg_plan p);
 
 /* Message for the last failing call on this thread ("" if none). */

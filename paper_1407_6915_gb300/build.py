@@ -40,14 +40,21 @@ def _compile(nvcc, src, obj, extra):
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
+def build(force: bool = False, verbose: bool = False, extra=None, debug: bool = False) -> str:
+    """Builds libfftseg.so, or with debug=True the self-checking variant
+    libfftseg_debug.so (-DFFTSEG_DEBUG: kernels check their shared-memory and
+    ring indices and report a bad one through fftseg_plan_check)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD + ("_debug" if debug else "")
+    lib_path = LIB[:-3] + "_debug.so" if debug else LIB
+    if debug:
+        extra = list(extra or []) + ["-DFFTSEG_DEBUG"]
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     newest_dep = max([os.path.getmtime(d) for d in _deps()] + [0.0])
     todo, objs = [], []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(build_dir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or not os.path.exists(o) or os.path.getmtime(o) < max(os.path.getmtime(s), newest_dep):
             todo.append((s, o))
@@ -56,16 +63,16 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
             futs = [ex.submit(_compile, nvcc, s, o, list(extra or [])) for s, o in todo]
             for f in futs:
                 f.result()
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if todo or not os.path.exists(lib_path):
+        tmp = lib_path + ".tmp%d" % os.getpid()
         cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib_path)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -22,6 +22,18 @@
 #define FDEV __device__ __forceinline__
 #define HDEV __host__ __device__ __forceinline__
 
+// Self-checking build (compiled with -DFFTSEG_DEBUG): FFTSEG_CHECK(cond, err)
+// is cond, and when cond is false it also sets bit 8 of *err, which
+// fftseg_plan_check reports.  The caller then keeps the access inside its
+// buffer (it is skipped or redirected), so a bad index is recorded, never
+// performed: nothing traps.  In the normal build it is `true` and costs
+// nothing.
+#ifdef FFTSEG_DEBUG
+#define FFTSEG_CHECK(cond, err) ((cond) ? true : (atomicOr((err), 8), false))
+#else
+#define FFTSEG_CHECK(cond, err) true
+#endif
+
 namespace fftseg {
 
 HDEV float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }

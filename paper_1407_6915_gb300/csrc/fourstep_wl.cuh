@@ -156,7 +156,8 @@ struct WlTw {
 // tw: stage-2 twiddles in shared memory, or (treg) the lane's own in registers.
 template <class PS, int S>
 FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int group, const float2 *tw,
-                  const WlTw<PS> *treg = nullptr, const float2 *wrow = nullptr, float2 wcol = float2{})
+                  const WlTw<PS> *treg = nullptr, const float2 *wrow = nullptr, float2 wcol = float2{},
+                  [[maybe_unused]] int *err = nullptr)
 {
     constexpr int P = PS::P, Q = PS::Q, ROWB = PS::ROWB;
     const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
@@ -166,7 +167,11 @@ FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int grou
     const uint32_t rb = pb + (uint32_t)(ROWB * j) + sw;
     // exchange rows phi(32 j + r) = 32 j + (r ^ j7)
     const uint32_t wb = pb + (uint32_t)(32 * ROWB * j + ROWB * j7) + sw;
-    auto at = [&](uint32_t off) -> float2 & { return *reinterpret_cast<float2 *>(Pc + off); };
+    // (self-checking build: every slot within this tile's buffer, 8-byte aligned)
+    auto at = [&](uint32_t off) -> float2 & {
+        if (!FFTSEG_CHECK(off - tb < (uint32_t)(PS::L * PS::W * 8) && (off & 7) == 0, err)) off = tb;
+        return *reinterpret_cast<float2 *>(Pc + off);
+    };
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = at(rb + ROWB * P * r);
     if (wrow) {  // the frame's window on rows j + P r of this column
@@ -295,7 +300,9 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                     // the tile's ring block was consumed: drop its lines from L2
                     constexpr int LINES = Sh::N2 * PB::W * 8 / 128;
                     const float2 *tile = a.ring + (int64_t)slab * N + (int64_t)rt * Sh::N2 * PB::W;
-                    for (int l = lane; l < LINES; l += 32) discard_l2_line(tile + (int64_t)l * 16);
+                    // (self-checking build: the block lies inside the ring)
+                    if (FFTSEG_CHECK(slab < a.nr * a.cs && rt < Sh::TSEG_B, a.err))
+                        for (int l = lane; l < LINES; l += 32) discard_l2_line(tile + (int64_t)l * 16);
                     __syncwarp();
                 }
                 pend[npend++] = doneB + s;
@@ -464,7 +471,7 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const int c = 2 * group + ((u >> 3) & 1), j = (u & 7) | ((u >> 4) << 3);
             float2 v[32];
             const float2 wcol = a.win_row ? __ldg(a.win_col + ct * PS::W + c) : float2{};
-            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA, TW_REG ? &treg : nullptr, a.win_row, wcol);
+            wl_line<PS, S>(v, Pc, tb, c, j, group, TWA, TW_REG ? &treg : nullptr, a.win_row, wcol, a.err);
             // times w_n^{j2 k1}, k1 = j + P m: w_n^{j2 j} w_n^{j2 P m} (scale folded in), into the ring
             const float2 *Fb = F + bb * PS::FT;
             const float2 f1 = Fb[((c >> 1) * PS::P + j) * 2 + (c & 1)];
@@ -486,7 +493,11 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                     // else (W_B a multiple of P, j < P): k1 / W_B = m P / W_B, k1 mod W_B = j + m P mod W_B
                     const int64_t off = PS::P >= WB ? (int64_t)mm * (PS::P / WB) * BLK
                                                     : (int64_t)(mm * PS::P / WB) * BLK + (mm * PS::P) % WB;
-                    dst[off] = twmul<S>(v[e * PS::P + r], wv);
+                    // (self-checking build: inside this segment's ring slab)
+                    if (FFTSEG_CHECK(dst + off - (a.ring + (int64_t)slab * N) < N &&
+                                         dst + off >= a.ring + (int64_t)slab * N && slab < a.nr * a.cs,
+                                     a.err))
+                        dst[off] = twmul<S>(v[e * PS::P + r], wv);
                 }
             (void)s;
         } else if (kind == KIND_B) {
@@ -497,8 +508,11 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const int group = tid / PS::GROUP, u = tid % PS::GROUP;
             const int c = 2 * group + ((u >> 3) & 1), j = (u & 7) | ((u >> 4) << 3);
             float2 v[32];
-            if constexpr (TW_REG) wl_line<PS, S>(v, Pc, tb, c, j, group, TWB, reinterpret_cast<const WlTw<PS> *>(&treg));
-            else wl_line<PS, S>(v, Pc, tb, c, j, group, TWB);
+            if constexpr (TW_REG)
+                wl_line<PS, S>(v, Pc, tb, c, j, group, TWB, reinterpret_cast<const WlTw<PS> *>(&treg), nullptr,
+                               float2{}, a.err);
+            else
+                wl_line<PS, S>(v, Pc, tb, c, j, group, TWB, nullptr, nullptr, float2{}, a.err);
             const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
             const uint32_t rb = tb + (uint32_t)((c / PS::PW) * PS::PANEL_BYTES) + (uint32_t)(PS::ROWB * j) +
                                 (uint32_t)(16 * (ch ^ ((j7 >> PS::SWZ_S) & PS::SWZ_M)) + 8 * h);
@@ -506,8 +520,11 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
 #pragma unroll
             for (int e = 0; e < PS::Q; ++e)
 #pragma unroll
-                for (int r = 0; r < PS::P; ++r)
-                    *reinterpret_cast<float2 *>(Pc + rb + PS::ROWB * (PS::P * e + 32 * r)) = v[e * PS::P + r];
+                for (int r = 0; r < PS::P; ++r) {
+                    const uint32_t off = rb + PS::ROWB * (PS::P * e + 32 * r);
+                    if (FFTSEG_CHECK(off - tb < Sh::TILE_BYTES, a.err))
+                        *reinterpret_cast<float2 *>(Pc + off) = v[e * PS::P + r];
+                }
             fence_proxy_async();  // read by the retirer's TMA store
         }
         __syncwarp();

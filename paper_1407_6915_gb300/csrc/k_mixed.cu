@@ -39,7 +39,7 @@ FDEV int divq(int x, int d, float rd)
 
 template <int R, int S>
 FDEV void mix_stage(const float2 *src, float2 *dst, int cnt, int n, int ns, float rm, float rns,
-                    const float2 *__restrict__ tw)
+                    const float2 *__restrict__ tw, [[maybe_unused]] int *err)
 {
     const int m = n / R;
     const int nb = cnt * m;
@@ -48,6 +48,8 @@ FDEV void mix_stage(const float2 *src, float2 *dst, int cnt, int n, int ns, floa
         const int j = g - seg * m;
         const int base = seg * n;
         float2 x[R];
+        // (self-checking build: the butterfly's points and outputs lie in the tile)
+        if (!FFTSEG_CHECK(seg < cnt && j < m && base + n <= cnt * n, err)) continue;
 #pragma unroll
         for (int r = 0; r < R; ++r) x[r] = src[base + j + r * m];
         int jq = j, k = 0;
@@ -59,6 +61,7 @@ FDEV void mix_stage(const float2 *src, float2 *dst, int cnt, int n, int ns, floa
         }
         dft<R, S>(x);
         const int o = base + jq * ns * R + k;
+        if (!FFTSEG_CHECK(o + (R - 1) * ns < base + n && k < ns, err)) continue;
 #pragma unroll
         for (int r = 0; r < R; ++r) dst[o + r * ns] = x[r];
     }
@@ -96,12 +99,12 @@ __global__ void __launch_bounds__(kMixT, 2) k_mixed(const __grid_constant__ Mixe
             const int ns = a.ns[st];
             const float rm = a.rm[st], rns = a.rns[st];
             switch (a.radix[st]) {
-                case 2: mix_stage<2, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
-                case 3: mix_stage<3, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
-                case 4: mix_stage<4, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
-                case 5: mix_stage<5, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
-                case 7: mix_stage<7, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
-                default: mix_stage<8, S>(src, dst, cnt, n, ns, rm, rns, tw); break;
+                case 2: mix_stage<2, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
+                case 3: mix_stage<3, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
+                case 4: mix_stage<4, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
+                case 5: mix_stage<5, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
+                case 7: mix_stage<7, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
+                default: mix_stage<8, S>(src, dst, cnt, n, ns, rm, rns, tw, a.err); break;
             }
             __syncthreads();
             float2 *tmp = src;

@@ -1345,6 +1345,8 @@ int fftseg_plan_check(fftseg_plan p)
     if (e != cudaSuccess) return cuda_error(e, "plan_check");
     if (flag) {
         cudaMemset(p->d_err, 0, sizeof(int));
+        if (flag & 8)  // only the self-checking build sets it
+            return set_error(FFTSEG_E_INVALID, "a kernel found an index out of its buffer (flag %d) and skipped it", flag);
         return set_error(FFTSEG_E_TIMEOUT, "a kernel gave up (flag %d): a bounded wait ran out or a shared buffer was misaligned", flag);
     }
     return FFTSEG_OK;
