@@ -43,15 +43,17 @@ FDEV void mix_stage(const float2 *src, float2 *dst, int cnt, int n, int ns, floa
 {
     const int m = n / R;
     const int nb = cnt * m;
+    // butterfly g = seg m + j, stepped by kMixT without a division per step
+    int seg = divq(threadIdx.x, m, rm);
+    int j = threadIdx.x - seg * m;
+    const int dseg = divq(kMixT, m, rm), dj = kMixT - dseg * m;
     for (int g = threadIdx.x; g < nb; g += kMixT) {
-        const int seg = divq(g, m, rm);
-        const int j = g - seg * m;
         const int base = seg * n;
         float2 x[R];
-        // (self-checking build: the butterfly's points and outputs lie in the tile)
-        if (!FFTSEG_CHECK(seg < cnt && j < m && base + n <= cnt * n, err)) continue;
+        // (self-checking build: the butterfly's points lie in the tile)
+        const bool ok = FFTSEG_CHECK(seg < cnt && j < m && base + n <= cnt * n, err);
 #pragma unroll
-        for (int r = 0; r < R; ++r) x[r] = src[base + j + r * m];
+        for (int r = 0; r < R; ++r) x[r] = ok ? src[base + j + r * m] : make_float2(0.f, 0.f);
         int jq = j, k = 0;
         if (ns > 1) {
             jq = divq(j, ns, rns);
@@ -61,9 +63,16 @@ FDEV void mix_stage(const float2 *src, float2 *dst, int cnt, int n, int ns, floa
         }
         dft<R, S>(x);
         const int o = base + jq * ns * R + k;
-        if (!FFTSEG_CHECK(o + (R - 1) * ns < base + n && k < ns, err)) continue;
+        if (FFTSEG_CHECK(o + (R - 1) * ns < base + n && k < ns, err)) {
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[o + r * ns] = x[r];
+            for (int r = 0; r < R; ++r) dst[o + r * ns] = x[r];
+        }
+        seg += dseg;
+        j += dj;
+        if (j >= m) {
+            j -= m;
+            ++seg;
+        }
     }
 }
 
@@ -77,20 +86,47 @@ __global__ void __launch_bounds__(kMixT, 2) k_mixed(const __grid_constant__ Mixe
         const int64_t left = a.nseg - t * spt;
         return (int)(left < spt ? left : spt);
     };
-    auto load = [&](int64_t t, float2 *dst) {
+    // A tile whose bytes start on a 16-byte boundary and are a multiple of 16
+    // (an even number of points) arrives by one bulk copy issued by thread 0
+    // and completed on an mbarrier; otherwise every thread issues 8-byte
+    // cp.async copies.
+    __shared__ __align__(8) uint64_t bar[2];
+    auto bulk_ok = [&](int64_t t) -> bool {
+        return ((t * spt * (int64_t)n) & 1) == 0 && ((count_of(t) * n) & 1) == 0;
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
+    auto load = [&](int64_t t, float2 *dst, int b) {
         const float2 *src = a.in + t * spt * (int64_t)n;
         const int count = count_of(t) * n;
-        for (int e = threadIdx.x; e < count; e += kMixT) cp_async8(dst + e, src + e, 8);
+        if (bulk_ok(t)) {
+            if (threadIdx.x == 0) {
+                fence_proxy_async();  // this buffer's earlier generic accesses before the copy
+                mbar_expect_tx(&bar[b], (uint32_t)(count * sizeof(float2)));
+                tma_load_1d(dst, src, (uint32_t)(count * sizeof(float2)), &bar[b]);
+            }
+        } else {
+            for (int e = threadIdx.x; e < count; e += kMixT) cp_async8(dst + e, src + e, 8);
+        }
     };
     int64_t t = blockIdx.x;
-    if (t < a.ntiles) load(t, buf0);
+    if (t < a.ntiles) load(t, buf0, 0);
     cp_async_commit();
     int cur = 0;
     for (; t < a.ntiles; t += gridDim.x) {
         const int64_t tn = t + gridDim.x;
-        if (tn < a.ntiles) load(tn, cur ? buf0 : buf1);
+        if (tn < a.ntiles) load(tn, cur ? buf0 : buf1, cur ^ 1);
         cp_async_commit();
         cp_async_wait<1>();  // this tile's copies (the group before the one just issued)
+        if (bulk_ok(t)) {
+            mbar_wait(&bar[cur], (phase >> cur) & 1, a.err);
+            phase ^= 1u << cur;
+        }
         __syncthreads();
         const int cnt = count_of(t);
         float2 *src = cur ? buf1 : buf0, *dst = buf2;
