@@ -456,17 +456,16 @@ def tc_split(peak):
             "sizes": out}
 
 
-def real_bench(peak):
+def real_bench(peak, sizes=None):
     """Real-signal segments (FLAG_REAL), forward: 4 GiB of float32 samples cut
     into n-point segments (n = 1024, the paper's record size, and 65536), to
     the n/2 + 1 bins of each segment.  Algorithmic bytes per segment: 4n in,
-    8 (n/2 + 1) out."""
+    8 (n/2 + 1) out.  `sizes`: other (n, segments) pairs (profiler captures)."""
     import torch
     import paper_1407_6915_gb300 as fs
     import siggen
     rows = []
-    for n in (1024, 65536):
-        B = (1 << 30) // n
+    for n, B in sizes or [(n, (1 << 30) // n) for n in (1024, 65536)]:
         h = torch.empty(B * n // 2, dtype=torch.complex64, pin_memory=True)
         siggen.fill_pointer(siggen.KIND_TONES, 6, 0, B * n // 2, h.data_ptr())
         x = h.cuda().view(torch.float32).view(B, n)
@@ -1015,11 +1014,20 @@ def main():
                          "profiler captures of their kernels)")
     ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="plan flags (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiler captures)")
+    ap.add_argument("--only", choices=["real"], default=None,
+                    help="run one extra measurement alone, at --n and --segments when given (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        peak, _ = peaks()
+        sizes = [(args.n, args.segments or (1 << 30) // args.n)] if args.segments else None
+        print(json.dumps({"only": args.only, args.only: real_bench(peak, sizes)}), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -1,15 +1,16 @@
-// Instantiations and launcher of the single-pass cluster kernel (n = 2^13..2^17).
+// Instantiations and launchers of the single-pass cluster kernel (n = 2^13..2^17),
+// complex segments and forward real-signal segments of 2n samples.
 #include "launch.h"
 
 namespace fftseg {
 
 namespace {
 
-template <int LOG_N1, int LOG_N2, int LOG_C, int S>
+template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false>
 cudaError_t cluster_t(const ClusterArgs &a, cudaStream_t st)
 {
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
-    auto k = k_cluster<LOG_N1, LOG_N2, LOG_C, S>;
+    auto k = k_cluster<LOG_N1, LOG_N2, LOG_C, S, RF>;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -78,6 +79,20 @@ cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a,
         case 15: return cluster_s<7, 8, 3>(sign, a, st);
         case 16: return lc == 4 ? cluster_s<8, 8, 4>(sign, a, st) : cluster_s<8, 8, 3>(sign, a, st);
         case 17: return cluster_s<8, 9, 4>(sign, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cluster_r2c(int log_n, int log_c, const ClusterArgs &a, cudaStream_t st)
+{
+    int l1, l2, lc;
+    if (!cluster_shape(log_n, log_c, &l1, &l2, &lc)) return cudaErrorInvalidValue;
+    switch (log_n) {
+        case 13: return cluster_t<6, 7, 1, -1, true>(a, st);
+        case 14: return cluster_t<7, 7, 2, -1, true>(a, st);
+        case 15: return cluster_t<7, 8, 3, -1, true>(a, st);
+        case 16: return lc == 4 ? cluster_t<8, 8, 4, -1, true>(a, st) : cluster_t<8, 8, 3, -1, true>(a, st);
+        case 17: return cluster_t<8, 9, 4, -1, true>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -15,12 +15,25 @@
 #pragma once
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "engine.cuh"
 #include "tc.cuh"
 
 namespace fftseg {
 
 namespace cg = cooperative_groups;
+
+// f(std::integral_constant<int, i>()) for i = I .. N-1 (indices usable as
+// template arguments inside f).
+template <int N, int I = 0, class F>
+FDEV void unroll_for(F &&f)
+{
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>());
+        unroll_for<N, I + 1>(f);
+    }
+}
 
 // ---------------------------------------------------------------- stage runner
 
@@ -362,6 +375,7 @@ struct ClusterArgs {
     const float2 *twA;  // stage twiddle tables, length N1
     const float2 *twB;  // stage twiddle tables, length N2
     const float2 *tw4;  // w_n^{k1 j2}, [N1][N2]
+    const float2 *rtw;  // real-signal segments: w_{2n}^k for k = 0 .. n/2
     int *err;
     int out_power;
     float scale;
@@ -420,7 +434,37 @@ struct ClusterShape {
 //    index of the last column stage): w_n^{j2 j} (per thread, kept in
 //    registers) times w_n^{j2 (N1/R) q} (table TR in shared memory), both
 //    exact table entries.
-template <int LOG_N1, int LOG_N2, int LOG_C, int S>
+// RF (forward real-signal segments, S = -1): a segment is 2n real samples
+// read as n complex values z[m] = x[2m] + i x[2m+1], and the output is the
+// n + 1 bins of their real DFT.  Bin k = k1 + N1 k2 needs A = Z[k] and
+// B = conj(Z[(n - k) mod n]), which sits in row (N1 - k1) mod N1 (column
+// N2 - 1 - k2 for k1 > 0, column -k2 mod N2 for k1 = 0).  So the row pass
+// deals rows out in mirror pairs (rf_row): CTA d takes rows d H + c and
+// their mirrors N1 - (d H + c), c < H = WB/2 (CTA 0: rows 0 and N1/2 are
+// their own mirrors), and the split is local to the CTA:
+//   X[k] = (A + B) / 2 + w_{2n}^k (-i) (A - B) / 2,   X[n] = Re Z[0] - Im Z[0].
+// Mirror-pair rows of the RF row pass: local row c of CTA d -> row k1, and back.
+template <int N1, int WB>
+FDEV int rf_row(int d, int c)
+{
+    constexpr int H = WB / 2;
+    if (c < H) return d * H + c;
+    const int m = d * H + c - H;
+    return m == 0 ? N1 / 2 : N1 - m;
+}
+template <int N1, int WB>
+FDEV void rf_place(int k1, int &d, int &c)
+{
+    // k1 < N1/2: m = k1, first half; k1 > N1/2: m = N1 - k1, second half;
+    // k1 = N1/2: m = 0, second half of CTA 0
+    constexpr int H = WB / 2;
+    const int hb = k1 >= N1 / 2;
+    const int m = (hb ? N1 - k1 : k1) & (N1 / 2 - 1);
+    d = m / H;
+    c = hb * H + (m & (H - 1));
+}
+
+template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false>
 __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, ClusterShape<LOG_N1, LOG_N2, LOG_C>::MINB)
     k_cluster(const __grid_constant__ ClusterArgs a)
 {
@@ -466,6 +510,29 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             wbase[b] = __ldg(a.tw4 + (int64_t)j * N2 + rank * WA + c);
         }
     }
+    // RF: this thread's local row of the row pass (fixed: T is a multiple of
+    // WB), its row k1 and its mirror's local row, and the split's factors
+    // -i (scale/2) w_{2n}^{k1 + N1 j} for the butterflies j of the last row
+    // stage (bin k = k1 + N1 (j + r N2/R) then takes that times w_{2R}^r)
+    static_assert(!RF || WB >= 2, "mirror pairs of rows per CTA");
+    using IRL = StageInfo<LOG_N2, StageInfo<LOG_N2, 0>::NSTAGES - 1>;
+    constexpr int RB = (E / T) / IRL::R;
+    const int rcl = tid & (WB - 1);
+    const int rk1 = RF ? rf_row<N1, WB>(rank, rcl) : 0;
+    const int rcm = (rk1 == 0 || rk1 == N1 / 2) ? rcl : rcl ^ (WB / 2);
+    float2 rpw[RF ? RB : 1];
+    if constexpr (RF) {
+        const float2 w1 = __ldg(a.rtw + rk1);  // k1 < N1 <= n/2
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            int c, j;
+            butterfly_coords<LOG_N2, Sh::LOG_WB, true, IRL::LOG_R>(tid + T * b, c, j);
+            const float2 w2 = __ldg(a.rtw + N1 * j);  // N1 j < n / R <= n/2
+            const float h = 0.5f * a.scale;
+            const float2 w = make_float2(h * (w1.x * w2.x - w1.y * w2.y), h * (w1.x * w2.y + w1.y * w2.x));
+            rpw[b] = make_float2(w.y, -w.x);  // times -i
+        }
+    }
     cl.sync();  // every peer's barriers are initialised before any copy reaches them
     const uint32_t x_remote0 = smem_u32(X) + (uint32_t)(rank * Sh::SLICE * sizeof(float2));
 
@@ -496,8 +563,10 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             const float2 w = TR[(k1 >> LOG_STEP) * WA + c];  // k1 = j + (N1/R) q
             const float2 wb = wbase[b];
             x = twmul<S>(x, make_float2(w.x * wb.x - w.y * wb.y, w.x * wb.y + w.y * wb.x));
-            const int qq = c * WB + (k1 & (WB - 1));
-            U[(k1 >> Sh::LOG_WB) * Sh::SLICE + qq + (qq >> Sh::PSB)] = x;
+            int d = k1 >> Sh::LOG_WB, cl = k1 & (WB - 1);
+            if constexpr (RF) rf_place<N1, WB>(k1, d, cl);
+            const int qq = c * WB + cl;
+            U[d * Sh::SLICE + qq + (qq >> Sh::PSB)] = x;
         });
         fence_proxy_async();      // these generic writes are read by the async-proxy copies below
         __syncthreads();          // U complete
@@ -520,13 +589,75 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             v, [&](int c, int i) { return X[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(c, i)]; });
         run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0, true, false, PREC_FP32, false, true>(v, X, TWB);
 
-        const int64_t obase = s * N + rank * WB;
-        scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
-            if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
-            const int64_t o = obase + (int64_t)k2 * N1 + c;
-            if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
-            else static_cast<float2 *>(a.out)[o] = x;
-        });
+        if constexpr (!RF) {
+            const int64_t obase = s * N + rank * WB;
+            scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
+                if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
+                const int64_t o = obase + (int64_t)k2 * N1 + c;
+                if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
+                else static_cast<float2 *>(a.out)[o] = x;
+            });
+        } else {
+            static_assert(!RF || S == -1, "real-signal segments: forward only");
+            // Bins pair up: k (column k2 < N2/2, i.e. r < R/2) with n - k (its
+            // mirror row's column N2 - 1 - k2, or -k2 mod N2 in row 0).  With
+            // A = Z[k], B = conj(Z[n - k]), P = (scale/2)(A + B) and
+            // Q = -i (scale/2) w_{2n}^k (A - B):  X[k] = P + Q, X[n - k] = conj(P - Q)
+            // (w_{2n}^{n-k} = -conj(w_{2n}^k)).  k = 0 gives X[0] and X[n];
+            // k = n/2 (row 0, column N2/2) pairs with itself.
+            // Element u = (b, r) of this thread is column k2 = j0 + dk2(u) of its
+            // row, dk2 = b T/WB + r N2/R; its slot and its partner's step with
+            // dk2 by whole multiples of 2^PSB (WB is one), so the padded slot
+            // index is linear in dk2.
+            static_assert(!RF || WB % (1 << Sh::PSB) == 0, "linear slots");
+            constexpr int SLOT_STEP = WB + (WB >> Sh::PSB);
+            auto dk2 = [](int b, int r) { return b * (T / WB) + (r << (LOG_N2 - IRL::LOG_R)); };
+            const int j0 = tid >> Sh::LOG_WB;
+            const int koff = rk1 == 0 ? N2 : N2 - 1;  // partner column koff - k2 (row 0: N2 at k2 = 0, unused)
+            const int wslot = smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(rcl, j0);
+            const int rslot = smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(rcm, koff - j0);
+            __syncthreads();  // the last row stage has read X: it now takes the partners' halves of Z
+            unroll_for<E / T>([&](auto uc) {
+                constexpr int u = decltype(uc)::value, b = u / IRL::R, r = u % IRL::R;
+                if constexpr (r >= IRL::R / 2) X[wslot + dk2(b, r) * SLOT_STEP] = v[u];
+            });
+            __syncthreads();  // every partner is in X
+            const int64_t ob = s * (N + 1);
+            const float h = 0.5f * scale;
+            const int kbase = rk1 + N1 * j0;
+            auto put = [&](int k, int km, float2 za, float2 zb, float2 w) {
+                const float2 P = make_float2(h * (za.x + zb.x), h * (za.y - zb.y));
+                const float dx = za.x - zb.x, dy = za.y + zb.y;
+                const float2 Q = make_float2(w.x * dx - w.y * dy, w.x * dy + w.y * dx);
+                const float2 xk = make_float2(P.x + Q.x, P.y + Q.y), xm = make_float2(P.x - Q.x, Q.y - P.y);
+                if (a.out_power) {
+                    float *Po = static_cast<float *>(a.out) + ob;
+                    Po[k] = power_of(xk);
+                    Po[km] = power_of(xm);
+                } else {
+                    float2 *Xo = static_cast<float2 *>(a.out) + ob;
+                    Xo[k] = xk;
+                    Xo[km] = xm;
+                }
+            };
+            unroll_for<E / T>([&](auto uc) {
+                constexpr int u = decltype(uc)::value, b = u / IRL::R, r = u % IRL::R;
+                if constexpr (r < IRL::R / 2) {
+                    float2 zb = X[rslot - dk2(b, r) * SLOT_STEP];
+                    const bool z0 = u == 0 && rk1 == 0 && j0 == 0;  // k = 0: its own partner, in v[0]
+                    if (z0) zb = v[0];
+                    const int k = kbase + N1 * dk2(b, r);
+                    put(k, (int)N - k, v[u], zb, rot32<(r * (16 / IRL::R)) & 15, -1>(rpw[b]));
+                    if constexpr (u == 0) {
+                        if (z0) {  // k = n/2 (column N2/2 of row 0): v[R/2], its own partner
+                            const int kh = (int)N / 2;
+                            put(kh, kh, v[IRL::R / 2], v[IRL::R / 2],
+                                rot32<(IRL::R / 2) * (16 / IRL::R) & 15, -1>(rpw[0]));
+                        }
+                    }
+                }
+            });
+        }
         cluster_arrive_relaxed();  // this thread's reads of X were consumed above
     }
     cluster_wait();

@@ -33,6 +33,9 @@ int pass_log_w(int log_l);
 // Single-pass cluster kernel for n = 2^log_n, 2^13..2^17; log_c selects the
 // cluster size where two are built (0 = default).
 cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a, cudaStream_t st);
+// Forward real-signal segments of 2^(log_n + 1) samples on the cluster kernel
+// (the split into the real DFT's bins in its epilogue; a.rtw, a.out_power, a.scale).
+cudaError_t launch_cluster_r2c(int log_n, int log_c, const ClusterArgs &a, cudaStream_t st);
 // Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
 bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
 

@@ -62,6 +62,15 @@ bool frames_fused(const fftseg_plan_s *p)
     return p->path == PATH_FRAMES && p->inner && p->inner->path == PATH_BLOCK &&
            p->inner->precision == FFTSEG_PREC_FP32;
 }
+
+// Forward real-signal plans whose n/2-point complex transform runs on the
+// block or the cluster kernel split the spectrum inside that kernel (one
+// pass, no intermediate).
+bool real_fused(const fftseg_plan_s *p)
+{
+    return p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner &&
+           (p->inner->path == PATH_BLOCK || p->inner->path == PATH_CLUSTER);
+}
 int ilog2(int64_t n)
 {
     int l = 0;
@@ -412,7 +421,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         }
         case PATH_REAL:
         case PATH_FRAMES: {
-            if (p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner->path == PATH_BLOCK) return 1;
+            if (real_fused(p)) return 1;
             if (frames_fused(p) || p->frames_wl) return 1;
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk)
@@ -686,6 +695,29 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             count_launches(1);
             return FFTSEG_OK;
         }
+        if (real_fused(p)) {
+            // n/2 = 2^13..2^17 on the cluster kernel: the split in its epilogue
+            const fftseg_plan_s *q = p->inner;
+            ClusterArgs a{};
+            const int64_t N1 = int64_t(1) << q->log_n1, N2 = int64_t(1) << q->log_n2;
+            const uint32_t WA = (uint32_t)(N2 >> q->log_c);
+            int rc = encode_tmap_3d(&a.tmap, d_in, N2, N1, nseg, N2 * 8, M * 8, WA, (uint32_t)N1);
+            if (rc != FFTSEG_OK) return rc;
+            a.in = static_cast<const float2 *>(d_in);
+            a.out = d_out;
+            a.nseg = nseg;
+            a.err = p->d_err;
+            a.twA = q->twA;
+            a.twB = q->twB;
+            a.tw4 = q->tw4a;
+            a.rtw = p->rtw;
+            a.out_power = power;
+            a.scale = p->scale;
+            cudaError_t e = launch_cluster_r2c(q->log_n, q->log_c, a, st);
+            if (e != cudaSuccess) return cuda_error(e, "real-signal cluster kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
         // otherwise chunks of rchunk segments: the complex FFT of n/2 points and
         // the split (forward) or join (inverse) pass, through an L2-sized intermediate
         for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
@@ -953,7 +985,7 @@ int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int n
         rc = upload(&p->rtw, h);
     }
     if (rc == FFTSEG_OK) {
-        e = cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
+        e = real_fused(p) ? cudaSuccess : cudaMalloc((void **)&p->rwork, (size_t)(cs * M) * sizeof(float2));
         if (e == cudaSuccess) e = cudaMalloc((void **)&p->d_err, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
         if (e != cudaSuccess) rc = cuda_error(e, "cudaMalloc(real-signal intermediate)");
@@ -1323,7 +1355,7 @@ int fftseg_plan_info(fftseg_plan p, int64_t info[6])
                   : int64_t(1) << p->log_n2;
     info[3] = p->path == PATH_BLUESTEIN ? (p->rwork ? p->rchunk * p->bm * 8 : 0)
               : p->path == PATH_FRAMES ? (p->rwork ? p->rchunk * p->n * 8 : 0)
-              : p->path == PATH_REAL ? p->rchunk * (p->n / 2) * 8
+              : p->path == PATH_REAL ? (p->rwork ? p->rchunk * (p->n / 2) * 8 : 0)
                                     : p->work ? p->work_segs * p->n * 8
                                               : (p->ring ? (int64_t)p->ring_nr * p->ring_cs * p->n * 8 : 0);
     info[4] = (p->path == PATH_REAL || p->path == PATH_FRAMES || p->path == PATH_BLUESTEIN) ? p->rchunk

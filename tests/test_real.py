@@ -72,6 +72,38 @@ def test_r2c_power(log_n):
     assert rel_l2(got.cpu().numpy(), X.real ** 2 + X.imag ** 2) <= 2 * tol_fp32(n)
 
 
+# forward plans whose n/2-point transform runs on the cluster kernel split the
+# spectrum in that kernel's epilogue (bins k and n/2 - k sit in different CTAs
+# of the cluster): every cluster shape, both outputs, batches smaller than the
+# grid's clusters and ragged ones, every segment compared
+@pytest.mark.parametrize("log_n,cflag", [(14, 0), (15, 0), (16, 0), (17, 3), (17, 4), (18, 4)])
+@pytest.mark.parametrize("out_kind,norm", [(fs.OUT_COMPLEX, fs.NORM_NONE), (fs.OUT_COMPLEX, fs.NORM_ORTHO),
+                                           (fs.OUT_POWER, fs.NORM_NONE)])
+def test_r2c_cluster_split(log_n, cflag, out_kind, norm):
+    n = 1 << log_n
+    B = 37
+    x = real_signal(900 + log_n + cflag, B, n)
+    flags = fs.FLAG_REAL | (fs.FLAG_CLUSTER_LOG2(cflag) if cflag else 0)
+    plan = fs.Plan(n, B, FWD, norm, out_kind=out_kind, flags=flags)
+    info = plan.info()
+    assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0, info
+    power = out_kind == fs.OUT_POWER
+    X = oracle.rfft(x, norm)
+    ref = X.real ** 2 + X.imag ** 2 if power else X
+    d = torch.from_numpy(x).cuda()
+    for nseg in (B, 1, 5):
+        dt = torch.float32 if power else torch.complex64
+        buf, got = guard(torch.empty(nseg, n // 2 + 1, dtype=dt, device="cuda"))
+        plan.exec(d, out=got, nseg=nseg)
+        torch.cuda.synchronize()
+        plan.check()
+        check_guard(buf)
+        g = got.cpu().numpy()
+        assert rel_l2(g, ref[:nseg]) <= (2 if power else 1) * tol_fp32(n), (nseg, rel_l2(g, ref[:nseg]))
+        if not power:
+            assert np.all(g[:, 0].imag == 0) and np.all(g[:, n // 2].imag == 0)
+
+
 @pytest.mark.parametrize("log_n", [2, 3, 6, 12, 13, 16, 20])
 @pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_BACKWARD, fs.NORM_ORTHO])
 def test_c2r_matches_oracle(log_n, norm):
