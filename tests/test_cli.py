@@ -94,8 +94,9 @@ def _free_port():
 
 
 def _rank(rank, world, port, argv, results):
+    # host-only ranks (gloo, a fake plan): no GPU is touched, also on a machine with fewer GPUs than ranks
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world), RANK=str(rank),
-                      LOCAL_RANK=str(rank))
+                      LOCAL_RANK=str(rank), CUDA_VISIBLE_DEVICES="")
     results[rank] = cli.main(argv, plan_factory=FakePlan)
 
 
