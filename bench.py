@@ -691,7 +691,6 @@ def tune_table():
 def serve_bench(peak, njobs=600, seed=5):
     """Poisson arrivals at 0.3/0.7/0.95 of the measured saturated throughput through the
     continuous-batching server (32 GB budget); p50/p99 submit-to-completion latency."""
-    import concurrent.futures as cf
     import numpy as np
     import torch
     import paper_1407_6915_gb300 as fs
@@ -716,34 +715,29 @@ def serve_bench(peak, njobs=600, seed=5):
     budget = 32 << 30
 
     def run(arrivals, subset=None):
+        # submit at the arrival times from this thread; each job's latency is
+        # the server's own submit-to-completion time, read once all are in
         srv = fs.Server(hbm_budget_bytes=budget, max_inflight_jobs=256)
         lat = [None] * len(jobs)
         pos = 0
+        ids = []
         t0 = time.perf_counter()
-        with cf.ThreadPoolExecutor(max_workers=512) as ex:
-            futs = []
-            for i, (n, nseg, direction, norm) in enumerate(jobs):
-                if subset is not None and i not in subset:
-                    continue
-                if arrivals is not None:
-                    wait = t0 + arrivals[i] - time.perf_counter()
-                    if wait > 0:
-                        time.sleep(wait)
-                sz = n * nseg
-                if pos + sz > ring_elems:
-                    pos = 0
-                out_ptr = ring.data_ptr() + 8 * pos
-                pos += sz
-                ts = time.perf_counter()
-                jid = srv.submit(x.data_ptr(), out_ptr, n, nseg, direction, norm)
-
-                def wait_one(jid=jid, ts=ts, i=i):
-                    done, st = srv.poll(jid, timeout_us=120_000_000)
-                    lat[i] = (time.perf_counter() - ts) if (done and st == fs.OK) else None
-
-                futs.append(ex.submit(wait_one))
-            for f in futs:
-                f.result()
+        for i, (n, nseg, direction, norm) in enumerate(jobs):
+            if subset is not None and i not in subset:
+                continue
+            if arrivals is not None:
+                wait = t0 + arrivals[i] - time.perf_counter()
+                if wait > 0:
+                    time.sleep(wait)
+            sz = n * nseg
+            if pos + sz > ring_elems:
+                pos = 0
+            out_ptr = ring.data_ptr() + 8 * pos
+            pos += sz
+            ids.append((i, srv.submit(x.data_ptr(), out_ptr, n, nseg, direction, norm)))
+        for i, jid in ids:
+            done, st, secs = srv.poll_latency(jid, timeout_us=120_000_000)
+            lat[i] = secs if (done and st == fs.OK) else None
         wall = time.perf_counter() - t0
         stats = srv.stats()
         srv.destroy()
@@ -783,6 +777,8 @@ def serve_bench(peak, njobs=600, seed=5):
     del ring, x
     torch.cuda.empty_cache()
     return {"jobs": njobs, "budget_bytes": budget, "per_length_class": per_class,
+            "latency": "submit-to-completion by the server's host clock (fftsrv_poll_latency); jobs submitted "
+                       "from one thread at their arrival times",
             "job_recipe": "n = 2^e, e uniform in 8..22; segments 2^U(0,12) capped at 2^28 samples per job; "
                           "50/50 forward / inverse(1/n); uniform[-1,1) input",
             "saturated_gflops": round(flops / wall_sat / 1e9, 1),
@@ -1014,7 +1010,7 @@ def main():
                          "profiler captures of their kernels)")
     ap.add_argument("--flags", type=lambda v: int(v, 0), default=0, help="plan flags (profiler captures)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg (profiler captures)")
-    ap.add_argument("--only", choices=["real"], default=None,
+    ap.add_argument("--only", choices=["real", "serve"], default=None,
                     help="run one extra measurement alone, at --n and --segments when given (profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -1025,8 +1021,12 @@ def main():
         import torch
         torch.cuda.set_device(0)
         peak, _ = peaks()
-        sizes = [(args.n, args.segments or (1 << 30) // args.n)] if args.segments else None
-        print(json.dumps({"only": args.only, args.only: real_bench(peak, sizes)}), flush=True)
+        if args.only == "real":
+            sizes = [(args.n, args.segments or (1 << 30) // args.n)] if args.segments else None
+            res = real_bench(peak, sizes)
+        else:
+            res = serve_bench(peak)
+        print(json.dumps({"only": args.only, args.only: res}), flush=True)
         return 0
     return run_ours(args)
 

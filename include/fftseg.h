@@ -412,6 +412,11 @@ int fftsrv_submit(fftsrv s, const fftsrv_job *job, uint64_t *job_id);
  * *job_status = the job's final status once it has completed, or
  * FFTSEG_E_TIMEOUT while it is still queued or running. */
 int fftsrv_poll(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status);
+/* As fftsrv_poll; once the job has completed, also *latency_us (if not NULL)
+ * = its time in the server by the host's steady clock, from fftsrv_submit
+ * accepting it to the completion callback of its last piece (so a caller
+ * that polls late still reads the job's own latency). */
+int fftsrv_poll_latency(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status, double *latency_us);
 /* Server counters: out[0] jobs submitted, out[1] completed, out[2] launches,
  * out[3] peak admitted bytes, out[4] queue depth now. */
 int fftsrv_stats(fftsrv s, int64_t out[5]);

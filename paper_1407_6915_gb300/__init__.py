@@ -103,6 +103,8 @@ _SIGS = {
     "fftsrv_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(SrvConfig)]),
     "fftsrv_submit": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(SrvJob), ctypes.POINTER(ctypes.c_uint64)]),
     "fftsrv_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int)]),
+    "fftsrv_poll_latency": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int),
+                                           ctypes.POINTER(ctypes.c_double)]),
     "fftsrv_stats": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)]),
     "fftsrv_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
@@ -395,6 +397,16 @@ class Server:
             return False, None
         check(rc, "fftsrv_poll")
         return True, st.value
+
+    def poll_latency(self, job_id, timeout_us=0):
+        """(done, job_status, latency_s): the job's submit-to-completion time
+        as the server's host clock saw it (None while queued or running)."""
+        st, lat = ctypes.c_int(0), ctypes.c_double(0.0)
+        rc = lib().fftsrv_poll_latency(self._h, job_id, int(timeout_us), ctypes.byref(st), ctypes.byref(lat))
+        if rc == E_TIMEOUT:
+            return False, None, None
+        check(rc, "fftsrv_poll_latency")
+        return True, st.value, lat.value * 1e-6
 
     def stats(self) -> dict:
         a = (ctypes.c_int64 * 5)()

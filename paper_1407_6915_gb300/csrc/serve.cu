@@ -162,6 +162,8 @@ struct Job {
     int status = FFTSEG_OK;
     bool admitted = false;
     bool done = false;
+    // host clock: fftsrv_submit accepted the job / its last piece was retired
+    std::chrono::steady_clock::time_point t_submit{}, t_done{};
 };
 
 struct Done {
@@ -251,6 +253,7 @@ void CUDART_CB on_done(void *arg)
             Job &jb = it->second;
             if (--jb.pieces_inflight == 0 && jb.next_seg == jb.j.nseg) {
                 jb.done = true;
+                jb.t_done = std::chrono::steady_clock::now();
                 s->inflight_jobs--;
                 s->completed++;
             }
@@ -399,6 +402,7 @@ void fftsrv_s::scheduler()
                 jb.status = rc;
                 if (--jb.pieces_inflight == 0 && !jb.done) {
                     jb.done = true;
+                    jb.t_done = std::chrono::steady_clock::now();
                     inflight_jobs--;
                     completed++;
                 }
@@ -505,6 +509,7 @@ int fftsrv_submit(fftsrv s, const fftsrv_job *job, uint64_t *job_id)
     if (job->norm < FFTSEG_NORM_NONE || job->norm > FFTSEG_NORM_ORTHO)
         return set_error(FFTSEG_E_INVALID, "fftsrv_submit: bad norm");
     Job jb;
+    jb.t_submit = std::chrono::steady_clock::now();
     jb.j = *job;
     jb.log_n = ilog2i(n);
     jb.seg_bytes = n * 8 * (job->d_in == job->d_out ? 1 : 2);
@@ -525,6 +530,11 @@ int fftsrv_submit(fftsrv s, const fftsrv_job *job, uint64_t *job_id)
 
 int fftsrv_poll(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status)
 {
+    return fftsrv_poll_latency(s, job_id, timeout_us, job_status, nullptr);
+}
+
+int fftsrv_poll_latency(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status, double *latency_us)
+{
     if (!s || !job_status) return set_error(FFTSEG_E_INVALID, "fftsrv_poll: NULL argument");
     std::unique_lock<std::mutex> lock(s->mu);
     auto it = s->jobs.find(job_id);
@@ -540,6 +550,8 @@ int fftsrv_poll(fftsrv s, uint64_t job_id, int64_t timeout_us, int *job_status)
     if (!it->second.done) return set_error(FFTSEG_E_TIMEOUT, "fftsrv_poll: job %llu still queued or running",
                                            (unsigned long long)job_id);
     *job_status = it->second.status;
+    if (latency_us)
+        *latency_us = std::chrono::duration<double, std::micro>(it->second.t_done - it->second.t_submit).count();
     s->jobs.erase(it);  // a finished job is reported once
     return FFTSEG_OK;
 }

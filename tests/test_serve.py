@@ -97,6 +97,28 @@ def test_poll_times_out_instead_of_blocking():
     srv.destroy()
 
 
+def test_poll_latency_is_the_jobs_own():
+    # a job polled long after it completed still reports its own time in the
+    # server (submit to completion), not the time until the poll
+    import time
+    srv = fs.Server(hbm_budget_bytes=1 << 33, max_inflight_jobs=8)
+    n, nseg = 1 << 16, 256
+    x = torch.zeros(nseg, n, dtype=torch.complex64, device="cuda")
+    y = torch.empty_like(x)
+    t0 = time.perf_counter()
+    a = srv.submit(x, y, n, nseg)
+    b = srv.submit(x, y, 256, 4)
+    done, st, lat_a = srv.poll_latency(a, timeout_us=30_000_000)
+    t_a = time.perf_counter() - t0
+    assert done and st == fs.OK and 0 < lat_a <= t_a
+    time.sleep(0.2)
+    done, st, lat_b = srv.poll_latency(b, timeout_us=30_000_000)
+    assert done and st == fs.OK and 0 < lat_b < 0.2 < time.perf_counter() - t0
+    with pytest.raises(fs.FFTSegError):
+        srv.poll_latency(a)  # reported once, as by poll
+    srv.destroy()
+
+
 def test_destroy_drains_queue():
     jobs = make_jobs(3)
     srv = fs.Server(hbm_budget_bytes=1 << 30, max_inflight_jobs=2)
