@@ -222,16 +222,24 @@ KERNEL_TU = {"four-step": ("k_fourstep.cu", "k_fourstep_wl.cu"), "cluster": ("k_
 
 
 def kernel_rev(path="four-step"):
-    """Hash of the device code of a path's kernel (every kernel header and the
-    path's translation unit): a DRAM-traffic figure only applies to the kernel
-    sources it was taken on."""
+    """Hash of the device code of a path's kernel (its translation units and
+    every header they include, transitively): a DRAM-traffic figure only
+    applies to the kernel sources it was taken on."""
     import hashlib
-    h = hashlib.sha1()
+    import re
     csrc = os.path.join(ROOT, "paper_1407_6915_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith(".cuh") or name in KERNEL_TU.get(path, ()):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    seen, todo = set(), list(KERNEL_TU.get(path, ()))
+    while todo:
+        name = todo.pop()
+        if name in seen or not os.path.exists(os.path.join(csrc, name)):
+            continue
+        seen.add(name)
+        with open(os.path.join(csrc, name)) as f:
+            todo += re.findall(r'^#include "([^"]+)"', f.read(), re.M)
+    h = hashlib.sha1()
+    for name in sorted(seen):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:12]
 
 
