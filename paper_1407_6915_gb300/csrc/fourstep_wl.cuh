@@ -76,6 +76,14 @@ struct FourStepWlArgs {
     const float2 *win_col;
     int stall;           // test only: segment 0's row tiles wait for one column tile more than
                          // exists, with a short spin limit, so that the bounded wait runs out
+    // interleaved units (ILV kernels): R transforms of n = N1 N2 points per
+    // segment of R n points, G = R / 32 = 2^ilv_log_g units of 32 each.  The
+    // input holds unit u = s G + b contiguously, column after column:
+    // point j1 N2 + j2 of transform 32 b + c at ((u N2 + j2) N1 + j1) 32 + c
+    // (tmA is that array as [u N2 + j2][j1][c]); bin k1 + N1 k2 of transform
+    // t goes to X[t + R (k1 + N1 k2)] of segment s
+    int ilv_r;
+    int ilv_log_g;
 };
 
 // One pass over lines of L = 2^LOG_L points in tiles of E = 2^LOG_E points.
@@ -103,17 +111,23 @@ struct WlPass {
     __host__ __device__ static constexpr uint32_t K(int x) { return (uint32_t)(ROWB * x + 16 * ((x >> SWZ_S) & SWZ_M)); }
 };
 
-template <int LOG_N1, int LOG_N2, int LOG_E, int NB, int MINB>
+// ILV: the kernel's unit is 32 interleaved transforms (see FourStepWlArgs):
+// a column tile is column j2 of all 32 of them and a row tile row k1 of all
+// 32, so that every tile's lines are the 32 transforms and its loads and
+// stores stay 256-byte runs.
+template <int LOG_N1, int LOG_N2, int LOG_E, int NB, int MINB, bool ILV = false>
 struct FourStepWlShape {
     using PA = WlPass<LOG_N1, LOG_E>;
     using PB = WlPass<LOG_N2, LOG_E>;
     static constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2;
     static constexpr int64_t N = (int64_t)N1 * N2;
+    static constexpr int64_t NS = ILV ? 32 * N : N;  // points of one unit (one ring slab)
     static constexpr int E = 1 << LOG_E;
     static constexpr int TC = E / 32;        // compute threads: 32 points each
     static constexpr int TT = TC + 64;       // plus a loader warp and a retirer warp
-    static constexpr int TSEG_A = N2 / PA::W;  // column tiles per segment
-    static constexpr int TSEG_B = N1 / PB::W;  // row tiles per segment
+    static constexpr int TSEG_A = ILV ? N2 : N2 / PA::W;  // column tiles per unit
+    static constexpr int TSEG_B = ILV ? N1 : N1 / PB::W;  // row tiles per unit
+    static_assert(!ILV || (PA::W == 32 && PB::W == 32), "interleaved units: tiles of 32 lines");
     static constexpr uint32_t TILE_BYTES = E * sizeof(float2);
     static constexpr uint32_t F_BYTES = PA::FT * sizeof(float2);
     static constexpr int TWA = PA::TW, TWB = LOG_N1 == LOG_N2 ? 0 : PB::TW;
@@ -200,15 +214,15 @@ FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int grou
     }
 }
 
-template <int LOG_N1, int LOG_N2, int LOG_E, int NB, int MINB, int S>
-__global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MINB>::TT, MINB)
+template <int LOG_N1, int LOG_N2, int LOG_E, int NB, int MINB, int S, bool ILV = false>
+__global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MINB, ILV>::TT, MINB)
     k_fourstep_wl(const __grid_constant__ FourStepWlArgs a)
 {
-    using Sh = FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MINB>;
+    using Sh = FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MINB, ILV>;
     using PA = typename Sh::PA;
     using PB = typename Sh::PB;
     constexpr int E = Sh::E, TC = Sh::TC, N1 = Sh::N1;
-    constexpr int64_t N = Sh::N;
+    constexpr int64_t NS = Sh::NS;
     extern __shared__ __align__(1024) float2 sm[];
     float2 *const P = sm;
     float2 *const F = P + NB * E;
@@ -287,7 +301,10 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                         for (int p = 0; p < PB::NPANEL; ++p)
 #pragma unroll
                             for (int q = 0; q < PB::NBOXY; ++q)
-                                tma_store_3d_hint(&a.tmO, rt * PB::W + p * PB::PW, q * 256, s,
+                                tma_store_3d_hint(&a.tmO,
+                                                  (ILV ? rt * a.ilv_r + (s & ((1 << a.ilv_log_g) - 1)) * 32
+                                                       : rt * PB::W) + p * PB::PW,
+                                                  q * 256, ILV ? s >> a.ilv_log_g : s,
                                                   reinterpret_cast<char *>(P + b * E) + p * PB::PANEL_BYTES +
                                                       q * 256 * PB::ROWB,
                                                   stream_policy);
@@ -299,7 +316,7 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                 if (valid) {
                     // the tile's ring block was consumed: drop its lines from L2
                     constexpr int LINES = Sh::N2 * PB::W * 8 / 128;
-                    const float2 *tile = a.ring + (int64_t)slab * N + (int64_t)rt * Sh::N2 * PB::W;
+                    const float2 *tile = a.ring + (int64_t)slab * NS + (int64_t)rt * Sh::N2 * PB::W;
                     // (self-checking build: the block lies inside the ring)
                     if (FFTSEG_CHECK(slab < a.nr * a.cs && rt < Sh::TSEG_B, a.err))
                         for (int l = lane; l < LINES; l += 32) discard_l2_line(tile + (int64_t)l * 16);
@@ -410,12 +427,15 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
 #pragma unroll
                                 for (int q = 0; q < PA::NBOXY; ++q) {
                                     char *box = dst + p * PA::PANEL_BYTES + q * 256 * PA::ROWB;
-                                    const int x = tile * PA::W + p * PA::PW;
+                                    // (ILV: column j2 = tile of the unit's 32 transforms, one
+                                    // contiguous 256 x 32 block)
+                                    const int x = (ILV ? 0 : tile * PA::W) + p * PA::PW;
                                     if (a.frame_rows)  // rows of the signal from the frame's start
                                         tma_load_2d_hint(box, &a.tmA, x, (int)s * a.frame_rows + q * 256, &full[b],
                                                          stream_policy);
                                     else
-                                        tma_load_3d_hint(box, &a.tmA, x, q * 256, (int)s, &full[b], stream_policy);
+                                        tma_load_3d_hint(box, &a.tmA, x, q * 256, ILV ? (int)s * Sh::N2 + tile : (int)s,
+                                                         &full[b], stream_policy);
                                 }
                             tma_load_1d(F + b * PA::FT, a.w4t + (int64_t)tile * PA::FT, Sh::F_BYTES, &full[b]);
                         } else {
@@ -477,11 +497,14 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
             const float2 f1 = Fb[((c >> 1) * PS::P + j) * 2 + (c & 1)];
             const float2 *f2p = Fb + PS::W * PS::P + (c >> 1) * 64 + (c & 1);
             // ring block layout [k1 / W_B][j2][k1 mod W_B], k1 = j + P m
+            // (ILV: [k1][j2][transform c of the unit])
             constexpr int WB = PB::W;
             constexpr int64_t BLK = (int64_t)Sh::N2 * WB;
             const int j2 = ct * PS::W + c;
-            float2 *row = a.ring + (int64_t)slab * N + (int64_t)j2 * WB;
-            float2 *dst = PS::P >= WB ? row + (int64_t)(j / WB) * BLK + (j % WB) : row + j;
+            float2 *row = a.ring + (int64_t)slab * NS + (int64_t)j2 * WB;
+            float2 *dst = ILV ? a.ring + (int64_t)slab * NS + ct * WB + c + (int64_t)j * BLK
+                          : PS::P >= WB ? row + (int64_t)(j / WB) * BLK + (j % WB)
+                                        : row + j;
 #pragma unroll
             for (int e = 0; e < PS::Q; ++e)
 #pragma unroll
@@ -491,11 +514,12 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                     const float2 wv = make_float2(f1.x * f2.x - f1.y * f2.y, f1.x * f2.y + f1.y * f2.x);
                     // P >= W_B: k1 / W_B = j / W_B + m P / W_B, k1 mod W_B = j mod W_B;
                     // else (W_B a multiple of P, j < P): k1 / W_B = m P / W_B, k1 mod W_B = j + m P mod W_B
-                    const int64_t off = PS::P >= WB ? (int64_t)mm * (PS::P / WB) * BLK
-                                                    : (int64_t)(mm * PS::P / WB) * BLK + (mm * PS::P) % WB;
+                    const int64_t off = ILV ? (int64_t)mm * PS::P * BLK
+                                        : PS::P >= WB ? (int64_t)mm * (PS::P / WB) * BLK
+                                                      : (int64_t)(mm * PS::P / WB) * BLK + (mm * PS::P) % WB;
                     // (self-checking build: inside this segment's ring slab)
-                    if (FFTSEG_CHECK(dst + off - (a.ring + (int64_t)slab * N) < N &&
-                                         dst + off >= a.ring + (int64_t)slab * N && slab < a.nr * a.cs,
+                    if (FFTSEG_CHECK(dst + off - (a.ring + (int64_t)slab * NS) < NS &&
+                                         dst + off >= a.ring + (int64_t)slab * NS && slab < a.nr * a.cs,
                                      a.err))
                         dst[off] = twmul<S>(v[e * PS::P + r], wv);
                 }

@@ -14,11 +14,11 @@ namespace {
 // 4-27 % slower at 2^17..2^20.)
 constexpr int kWlLogE = 13, kWlNb = 3, kWlMinB = 1;
 
-template <int LOG_N1, int LOG_N2, int S>
+template <int LOG_N1, int LOG_N2, int S, bool ILV = false>
 cudaError_t wl_t(const FourStepWlArgs &a, cudaStream_t st)
 {
-    using Sh = FourStepWlShape<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB>;
-    auto k = k_fourstep_wl<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB, S>;
+    using Sh = FourStepWlShape<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB, ILV>;
+    auto k = k_fourstep_wl<LOG_N1, LOG_N2, kWlLogE, kWlNb, kWlMinB, S, ILV>;
     // per device: the occupancy of this instantiation (the grid is the
     // resident CTAs of the GPU the launch goes to)
     static int per_sm_dev[kMaxDevices] = {};  // per instantiation and device
@@ -55,6 +55,11 @@ bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e)
     *log_n2 = log_n / 2;
     *log_e = kWlLogE;
     return true;
+}
+
+cudaError_t launch_fourstep_wl_ilv(int sign, const FourStepWlArgs &a, cudaStream_t st)
+{
+    return sign < 0 ? wl_t<8, 8, -1, true>(a, st) : wl_t<8, 8, 1, true>(a, st);
 }
 
 cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st)

@@ -28,6 +28,12 @@ int block_segments_per_cta(int log_n);
 // One pass of the two-pass path over lines of length 2^log_l (16..4096),
 // interleaved tiles of 2^lines_log_w(log_l) lines; `units` CTAs.
 cudaError_t launch_pass(int log_l, int sign, const LinesArgs &a, int64_t units, cudaStream_t st);
+// The outer radix-R pass (R = 2^log_r, 32..256) of the interleaved four-step
+// for n = R * 2^16 (k_lines, columns of R points at stride 2^16, contiguous
+// output tiles).
+cudaError_t launch_outer_pass(int log_r, int sign, const LinesArgs &a, int64_t units, cudaStream_t st);
+// Columns j per tile of that pass.
+int outer_pass_columns(int log_r);
 int pass_log_w(int log_l);
 
 // Single-pass cluster kernel for n = 2^log_n, 2^13..2^17; log_c selects the
@@ -56,6 +62,9 @@ cudaError_t launch_fourstep_hw(int sign, const FourStepHwArgs &a, cudaStream_t s
 // column and row tiles, loader and retirer warps, swizzled TMA tiles.
 struct FourStepWlArgs;
 cudaError_t launch_fourstep_wl(int log_n, int sign, const FourStepWlArgs &a, cudaStream_t st);
+// The same kernel at n = 2^16 over interleaved units of 32 transforms
+// (a.ilv_r transforms per segment, a.nseg units).
+cudaError_t launch_fourstep_wl_ilv(int sign, const FourStepWlArgs &a, cudaStream_t st);
 // Factorisation n = N1 x N2 and log2 of the tile size of the lane-line kernel.
 bool fourstep_wl_shape(int log_n, int *log_n1, int *log_n2, int *log_e);
 // Real-signal segments (k_real.cu): the pass between a length-n real DFT and

@@ -44,6 +44,13 @@ bool uses_fourstep_wl(const fftseg_plan_s *p)
     return lane_kernels_apply(p) && p->log_n >= 16 && p->log_n <= 20 &&
            !(p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
 }
+// n = 2^21..2^24: the outer radix-R pass and the lane-line kernel over
+// interleaved transforms of 2^16 points (two HBM passes).
+bool uses_fourstep_ilv(const fftseg_plan_s *p)
+{
+    return lane_kernels_apply(p) && p->log_n >= 21 && p->log_n <= 24 &&
+           !(p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
+}
 // n = 256 x 256 on request: the warp-line kernel (fourstep_hw.cuh).
 bool uses_fourstep_hw(const fftseg_plan_s *p)
 {
@@ -226,12 +233,16 @@ int build_fourstep_wl(fftseg_plan p)
         // pair's two columns side by side (so that the two lines a half-warp
         // holds read adjacent entries): [wa/2][P1][2] w_n^{j2 j}, then
         // [wa/2][32][2] scale * w_n^{j2 P1 m}
+        // (interleaved units: column tile j2 holds column j2 of 32 transforms,
+        // so every column of tile j2 takes the factors of j2)
         const int64_t ft = wa * (p1 + 32);
-        std::vector<float2> h((size_t)(n2 / wa * ft));
+        const int64_t ntile = p->wl_ilv ? n2 : n2 / wa;
+        std::vector<float2> h((size_t)(ntile * ft));
         std::vector<float2> t1((size_t)p1), t2(32);
-        for (int64_t j2 = 0; j2 < n2; ++j2) {
-            float2 *t = h.data() + (j2 / wa) * ft;
-            const int64_t col = j2 % wa, pr = col >> 1, hc = col & 1;
+        for (int64_t tc = 0; tc < ntile * wa; ++tc) {
+            const int64_t j2 = p->wl_ilv ? tc / wa : tc;
+            float2 *t = h.data() + (tc / wa) * ft;
+            const int64_t col = tc % wa, pr = col >> 1, hc = col & 1;
             host_roots(t1.data(), p1, p->n, j2);
             host_roots(t2.data(), 32, p->n, j2 * p1);
             for (int64_t j = 0; j < p1; ++j) t[(pr * p1 + j) * 2 + hc] = t1[(size_t)j];
@@ -240,20 +251,69 @@ int build_fourstep_wl(fftseg_plan p)
         }
         if ((rc = upload(&p->w4t, h))) return rc;
     }
-    const int64_t chunk = (int64_t)env_int("FFTSEG_WL_CHUNK_MB", 24, 1, 64) << 20;
-    int64_t cs = chunk / (p->n * 8);
+    // (interleaved units of 16 MiB: two per chunk measured 6 % faster than one)
+    const int64_t chunk = (int64_t)env_int("FFTSEG_WL_CHUNK_MB", p->wl_ilv ? 32 : 24, 1, 64) << 20;
+    const int64_t slab = p->n * (p->wl_ilv ? 32 : 1);  // points of one unit
+    int64_t cs = chunk / (slab * 8);
     if (cs < 1) cs = 1;
     if (cs > p->batch) cs = p->batch;
     p->ring_cs = (int)cs;
     p->wl_la = env_int("FFTSEG_WL_LOOKAHEAD", 1, 1, 4);
     p->ring_nr = p->wl_la + 2;
-    cudaError_t e = cudaMalloc((void **)&p->ring, (size_t)(p->ring_nr * cs * p->n) * sizeof(float2));
+    cudaError_t e = cudaMalloc((void **)&p->ring, (size_t)(p->ring_nr * cs * slab) * sizeof(float2));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(ring)");
     const int64_t nc = (p->batch + cs - 1) / cs;
     p->ctr_count = 1 + 2 * nc * cs;
     e = cudaMalloc((void **)&p->ctr, (size_t)p->ctr_count * sizeof(int));
     if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(counters)");
     return FFTSEG_OK;
+}
+
+// n = R * M, M = 2^16, R = 2^(log2 n - 16) = 32..256 (decimation in
+// frequency over the outer index): the outer pass forms, for every j < M,
+//   Y_t[j] = w_n^{j t} sum_{t'} x[j + M t'] w_R^{t' t},   t < R,
+// written interleaved (Y_t[j] at R j + t); the lane-line plan of M points
+// then transforms each Y_t, 32 at a time, and writes bin k of Y_t to
+// X[t + R k].  Both passes stream the segment once: 32 bytes of HBM traffic
+// per point.  Work in chunks of segments through a 512 MiB workspace.
+int build_fourstep_ilv(fftseg_plan p)
+{
+    constexpr int kLogM = 16;
+    constexpr int64_t kIlvWorkBytes = int64_t(512) << 20;
+    const int log_r = p->log_n - kLogM;
+    const int64_t R = int64_t(1) << log_r, M = int64_t(1) << kLogM;
+    p->path = PATH_FOURSTEP;
+    p->ilv_log_r = log_r;
+    p->log_n1 = log_r;
+    p->log_n2 = kLogM;
+    int rc;
+    if ((rc = stage_table(&p->twA, R))) return rc;
+    // w_n^{j t} = [t mod 16][j] x [t div 16][j]
+    if ((rc = fourstep_table(&p->tw4a, p->n, 16, 1, M))) return rc;
+    if ((rc = fourstep_table(&p->tw4b, p->n, R / 16, 16, M))) return rc;
+    int64_t segs = kIlvWorkBytes / (p->n * 8);
+    if (segs < 1) segs = 1;
+    if (segs > p->batch) segs = p->batch;
+    p->work_segs = segs;
+    cudaError_t e = cudaMalloc((void **)&p->work, (size_t)(segs * p->n) * sizeof(float2));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(workspace)");
+    fftseg_plan q = new (std::nothrow) fftseg_plan_s();
+    if (!q) return set_error(FFTSEG_E_NOMEM, "plan_create: host allocation failed");
+    p->inner = q;
+    q->device = p->device;
+    q->n = M;
+    q->log_n = kLogM;
+    q->batch = segs * (R / 32);  // units of 32 interleaved transforms
+    q->direction = p->direction;
+    q->norm = p->norm;
+    q->precision = p->precision;
+    q->out_kind = p->out_kind;
+    q->scale = p->scale;  // the whole transform's scale, folded into the column factors
+    q->wl_ilv = true;
+    e = cudaMalloc((void **)&q->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(q->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_error(e, "cudaMalloc(status flag)");
+    return build_fourstep_wl(q);
 }
 
 // Persistent four-step: ring, counters, stage tables and the two factor
@@ -264,6 +324,7 @@ int build_fourstep(fftseg_plan p)
         return set_error(FFTSEG_E_UNSUPPORTED,
                          "plan_create: the warp-line four-step kernel runs FP32 complex output at n = 2^16");
     if (uses_fourstep_wl(p)) return build_fourstep_wl(p);
+    if (uses_fourstep_ilv(p)) return build_fourstep_ilv(p);
     int l1, l2, lwa, lwb;
     if (!fourstep_shape(p->log_n, &l1, &l2, &lwa, &lwb))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: the four-step path needs n in [2^14, 2^24]");
@@ -362,7 +423,8 @@ int build_fp32(fftseg_plan p)
     // (at 2^24 with complex output the two-pass path measured 8 % faster than
     // the persistent four-step: a segment's 128 MiB intermediate cannot stay
     // in L2, so both make two HBM passes)
-    const bool twopass_24 = ln == 24 && p->out_kind == FFTSEG_OUT_COMPLEX;
+    // (complex FP32 output at 2^21..2^24 runs the interleaved four-step instead)
+    const bool twopass_24 = ln == 24 && p->out_kind == FFTSEG_OUT_COMPLEX && !uses_fourstep_ilv(p);
     if (!force2 && want_c == 0 && !twopass_24 && (ln >= 17 || (ln == 16 && p->out_kind == FFTSEG_OUT_COMPLEX)))
         return build_fourstep(p);
     if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
@@ -408,7 +470,7 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
         case PATH_BLOCK:
         case PATH_CLUSTER: return 1;
         case PATH_TWOPASS: return 2 * ((nseg + p->work_segs - 1) / p->work_segs);
-        case PATH_FOURSTEP: return 1;
+        case PATH_FOURSTEP: return p->ilv_log_r ? 2 * ((nseg + p->work_segs - 1) / p->work_segs) : 1;
         case PATH_MIXED: return 1;
         case PATH_BLUESTEIN: {
             if (blue_fused(p)) return 1;
@@ -547,6 +609,84 @@ int exec_fourstep_wl(fftseg_plan p, const void *in, void *d_out, int64_t nseg, c
     e = launch_fourstep_wl(p->log_n, p->direction, a, st);
     if (e != cudaSuccess) return cuda_error(e, "four-step kernel launch");
     count_launches(1);
+    return FFTSEG_OK;
+}
+
+// The interleaved four-step (build_fourstep_ilv) on nseg segments, chunk by
+// chunk: the outer pass into the workspace, then the lane-line kernel.
+int exec_fourstep_ilv(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaStream_t st)
+{
+    const int log_r = p->ilv_log_r;
+    const int64_t n = p->n, R = int64_t(1) << log_r, M = n >> log_r;
+    const int64_t W = outer_pass_columns(log_r);  // columns per outer tile
+    const fftseg_plan_s *q = p->inner;
+    const int64_t n1 = 256, n2 = 256;
+    for (int64_t s0 = 0; s0 < nseg; s0 += p->work_segs) {
+        const int64_t cnt = nseg - s0 < p->work_segs ? nseg - s0 : p->work_segs;
+        LinesArgs A{};  // Y_t[j] = w_n^{j t} DFT_R over t' of x[j + M t'], stored unit by unit
+        A.in = static_cast<const float2 *>(d_in) + s0 * n;
+        A.out = p->work;
+        A.tiles_per_seg = M / W;
+        A.nseg = cnt;
+        A.in_seg = n;
+        A.out_seg = n;
+        A.in_tile = W;
+        A.out_tile = W * R;
+        A.in_cs = 1;
+        A.in_is = M;
+        A.out_cs = R;
+        A.out_is = 1;
+        A.twL = p->twA;
+        A.tw4a = p->tw4a;
+        A.tw4b = p->tw4b;
+        A.tw_ncols = M;
+        A.tw_log_k = 4;
+        A.out_ilv = 1;
+        A.ilv_n1 = n1;
+        A.ilv_n2 = n2;
+        A.ilv_blk = 32 * M;
+        A.scale = 1.f;
+        cudaError_t e = launch_outer_pass(log_r, p->direction, A, cnt * (M / W), st);
+        if (e != cudaSuccess) return cuda_error(e, "interleaved four-step: outer pass launch");
+        count_launches(1);
+        // units of 32 transforms: unit u = s G + b, transforms 32 b .. 32 b + 31 of segment s
+        const int64_t units = cnt * (R / 32);
+        const int cs = (int)(units < q->ring_cs ? units : q->ring_cs);
+        const int64_t slabs = (int64_t)q->ring_nr * cs, ns = 32 * M;
+        FourStepWlArgs a{};
+        // the workspace as [u N2 + j2][j1][transform c]
+        int rc = encode_tmap_3d_swz(&a.tmA, p->work, 32, n1, units * n2, 32 * 8, n1 * 32 * 8, 16, 256, 8, 128);
+        if (rc == FFTSEG_OK) {
+            // ring blocks [slab][k1][j2][transform]
+            const int64_t dims[4] = {32, n2, n1, slabs};
+            const int64_t strides[3] = {32 * 8, n2 * 32 * 8, ns * 8};
+            const uint32_t box[4] = {16, 256, 1, 1};
+            rc = encode_tmap(&a.tmB, q->ring, 4, dims, strides, box, 8, 128);
+        }
+        if (rc == FFTSEG_OK)  // X[t + R (k1 + N1 k2)] as [segment][k2][R k1 + t]
+            rc = encode_tmap_3d_swz(&a.tmO, static_cast<float2 *>(d_out) + s0 * n, n1 * R, n2, cnt, n1 * R * 8,
+                                    n * 8, 16, 256, 8, 128);
+        if (rc != FFTSEG_OK) return rc;
+        const int64_t nc = (units + cs - 1) / cs;
+        a.ring = q->ring;
+        a.twA = q->twA;
+        a.twB = q->twA;
+        a.w4t = q->w4t;
+        a.ctr = q->ctr;
+        a.err = q->d_err;
+        a.nseg = units;
+        a.nchunks = (int)nc;
+        a.cs = cs;
+        a.nr = q->ring_nr;
+        a.la = q->wl_la;
+        a.ilv_r = (int)R;
+        a.ilv_log_g = log_r - 5;
+        e = cudaMemsetAsync(q->ctr, 0, (size_t)(1 + 2 * nc * cs) * sizeof(int), st);
+        if (e != cudaSuccess) return cuda_error(e, "four-step counter reset");
+        e = launch_fourstep_wl_ilv(p->direction, a, st);
+        if (e != cudaSuccess) return cuda_error(e, "interleaved four-step: lane-line launch");
+        count_launches(1);
+    }
     return FFTSEG_OK;
 }
 
@@ -837,6 +977,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             return FFTSEG_OK;
         }
         case PATH_FOURSTEP: {
+            if (p->ilv_log_r) return exec_fourstep_ilv(p, in, d_out, nseg, st);
             // a batch smaller than a chunk runs as one chunk of its own size, so
             // that the persistent kernels do no work for absent segments
             const int cs = (int)(nseg < p->ring_cs ? nseg : p->ring_cs);

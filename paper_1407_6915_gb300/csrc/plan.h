@@ -53,6 +53,12 @@ struct fftseg_plan_s {
     float2 *w4 = nullptr, *w4hi = nullptr;
     float2 *w4t = nullptr;  // the warp-line and lane-line kernels' factors, per column tile
     int wl_la = 0;          // lane-line kernel: chunks of lookahead of column over row passes
+    // n = 2^21..2^24 (FP32, complex output): n = R * 2^16; the outer radix-R
+    // pass writes the R transforms of 2^16 points interleaved into `work`, and
+    // `inner`, a lane-line plan of 2^16 points over units of 32 interleaved
+    // transforms (wl_ilv), finishes them
+    int ilv_log_r = 0;
+    bool wl_ilv = false;
     int w4_log_k = 0;
     int log_wa = 0, log_wb = 0;
     // real-signal plans (FFTSEG_FLAG_REAL): a complex plan of n/2 points
