@@ -391,7 +391,9 @@ int fftseg_noalloc_check(void);
  */
 typedef struct fftsrv_s *fftsrv;
 typedef struct {
-    int64_t hbm_budget_bytes; /* bytes of job input+output that may be in flight */
+    int64_t hbm_budget_bytes; /* bytes of job input+output that may be in flight (the resident
+                                 plans' own scratch, made once per length, direction, norm
+                                 and lane, comes on top) */
     int max_inflight_jobs;
     fftseg_stream_t stream;   /* NULL: the server creates its own streams (four lanes for
                                  large jobs); else large jobs run in order on this stream */
