@@ -1,6 +1,6 @@
 """The self-checking build (-DFFTSEG_DEBUG, libfftseg_debug.so): the
-lane-line four-step and mixed-radix kernels check every shared-memory, ring
-and tile index they use and report a bad one through fftseg_plan_check
+lane-line four-step (also over interleaved units, 2^21..2^24) and
+mixed-radix kernels check every shared-memory, ring and tile index they use and report a bad one through fftseg_plan_check
 instead of performing it.  On valid inputs the checked build must give the
 release build's bits and report nothing."""
 import ctypes
@@ -45,7 +45,8 @@ def run_debug(L, make, x, out_shape):
     return y.cpu().numpy()
 
 
-@pytest.mark.parametrize("n,B", [(1 << 16, 70), (1 << 17, 40), (1 << 20, 9), (1000, 41), (3125, 5)])
+@pytest.mark.parametrize("n,B", [(1 << 16, 70), (1 << 17, 40), (1 << 20, 9), (1 << 21, 33), (1 << 24, 5), (1000, 41),
+                                 (3125, 5)])
 def test_checked_build_matches_release_bits(dbg, n, B):
     x = torch.from_numpy(siggen.tones(2000 + n % 997, B * n).reshape(B, n)).cuda()
     got = run_debug(dbg, lambda h: dbg.fftseg_plan_create(h, n, B, fs.FORWARD, fs.NORM_NONE, 0, 0, 0), x, (B, n))
