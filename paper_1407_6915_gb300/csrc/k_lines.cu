@@ -116,42 +116,6 @@ cudaError_t launch_block(int log_n, int sign, int prec, const BlockArgs &a, cuda
     }
 }
 
-// The outer pass of the interleaved four-step (n = R * 2^16): tiles of
-// 4096 / R columns j of R points each (stride 2^16), line-interleaved, 16
-// points per thread, the output staged for 256-byte runs.  (8192-point
-// tiles, 256-byte runs along j at R = 256, measured 31 % slower.)
-template <int LOG_R, int S>
-cudaError_t outer_t(const LinesArgs &a, int64_t units, cudaStream_t st)
-{
-    constexpr int LOG_E = 12;
-    constexpr int LOG_W = LOG_E - LOG_R, T = (1 << LOG_E) / 16;
-    auto k = k_lines<LOG_R, LOG_W, true, S, T>;
-    const size_t smem = (size_t)smem_slots<LOG_R, LOG_W, 4>() * sizeof(float2);
-    static bool configured_dev[kMaxDevices] = {};  // per instantiation and device
-    bool &configured = configured_dev[current_device_slot()];
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
-    if (units == 0) return cudaSuccess;
-    k<<<(unsigned)units, T, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-int outer_pass_columns(int log_r) { return 1 << (12 - log_r); }
-
-cudaError_t launch_outer_pass(int log_r, int sign, const LinesArgs &a, int64_t units, cudaStream_t st)
-{
-    switch (log_r) {
-        case 5: return sign < 0 ? outer_t<5, -1>(a, units, st) : outer_t<5, 1>(a, units, st);
-        case 6: return sign < 0 ? outer_t<6, -1>(a, units, st) : outer_t<6, 1>(a, units, st);
-        case 7: return sign < 0 ? outer_t<7, -1>(a, units, st) : outer_t<7, 1>(a, units, st);
-        case 8: return sign < 0 ? outer_t<8, -1>(a, units, st) : outer_t<8, 1>(a, units, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 #define FFTSEG_PASS_CASE(LL) \
     case LL: return sign < 0 ? pass_t<LL, -1>(a, units, st) : pass_t<LL, 1>(a, units, st);
 

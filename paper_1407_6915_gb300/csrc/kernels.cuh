@@ -206,13 +206,6 @@ struct LinesArgs {
     int tw_log_k;
     int in_staged;              // 1: load through shared memory, coalesced along the line (in_is == 1)
     int out_power;              // 1: store |X|^2 as float
-    // 1 (CFAST tiles, complex output, lines j = a segment's points j1 ilv_n2 + j2,
-    // one j1 per tile): the outer pass of the interleaved four-step.  Point t of
-    // line j goes to (t / 32) ilv_blk + (j2 ilv_n1 + j1) 32 + t mod 32 of the
-    // segment (its 32-transform unit, column j2, row j1); the tile is staged
-    // line-major in shared memory and stored in 256-byte runs
-    int out_ilv;
-    int64_t ilv_n1, ilv_n2, ilv_blk;
     float scale;
 };
 
@@ -250,8 +243,6 @@ __global__ void __launch_bounds__(T) k_lines(const LinesArgs a)
     run_stages<LOG_L, LOG_W, CFAST, S, T, PS, 0>(v, sm, a.twL);
 
     const float scale = a.scale;
-    const bool contig = CFAST && a.out_ilv;
-    if (contig) __syncthreads();  // the last stage's reads of sm are done: it takes the output tile
     scatter_last<LOG_L, LOG_W, CFAST, T>(v, [&](int c, int i, float2 x) {
         if (!CFAST && line0 + c >= a.nseg) return;
         if (a.tw4a) {  // four-step twiddle w_n^{col * k1}, k1 = i
@@ -264,29 +255,10 @@ __global__ void __launch_bounds__(T) k_lines(const LinesArgs a)
             x = twmul<S>(x, w);
         }
         if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);
-        if (contig) {  // line-major, one pad slot per line
-            sm[c * (L + 1) + i] = x;
-            return;
-        }
         const int64_t o = out_base + c * a.out_cs + i * a.out_is;
         if (a.out_power) static_cast<float *>(a.out)[o] = power_of(x);
         else static_cast<float2 *>(a.out)[o] = x;
     });
-    if (contig) {
-        static_assert(!CFAST || W * (L + 1) <= E + (E >> PS) + 1, "line-major output tile in sm");
-        static_assert(!CFAST || L % 32 == 0 || L < 32, "32-point runs of a line");
-        __syncthreads();
-        if constexpr (L >= 32) {
-            const int64_t jt = tile * W, j1 = jt / a.ilv_n2, j20 = jt - j1 * a.ilv_n2;
-            float2 *o = static_cast<float2 *>(a.out) + seg * a.out_seg + j20 * a.ilv_n1 * 32 + j1 * 32;
-#pragma unroll
-            for (int q = 0; q < V; ++q) {
-                const int e = threadIdx.x + T * q;  // e = (blk W + c) 32 + tl
-                const int tl = e & 31, c = (e >> 5) & (W - 1), blk = e >> (5 + LOG_W);
-                o[blk * a.ilv_blk + (int64_t)c * a.ilv_n1 * 32 + tl] = sm[c * (L + 1) + blk * 32 + tl];
-            }
-        }
-    }
 }
 
 // --------------------------------------------------------------------- k_block

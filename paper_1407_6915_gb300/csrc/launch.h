@@ -28,12 +28,18 @@ int block_segments_per_cta(int log_n);
 // One pass of the two-pass path over lines of length 2^log_l (16..4096),
 // interleaved tiles of 2^lines_log_w(log_l) lines; `units` CTAs.
 cudaError_t launch_pass(int log_l, int sign, const LinesArgs &a, int64_t units, cudaStream_t st);
-// The outer radix-R pass (R = 2^log_r, 32..256) of the interleaved four-step
-// for n = R * 2^16 (k_lines, columns of R points at stride 2^16, contiguous
-// output tiles).
-cudaError_t launch_outer_pass(int log_r, int sign, const LinesArgs &a, int64_t units, cudaStream_t st);
-// Columns j per tile of that pass.
-int outer_pass_columns(int log_r);
+// The interleaved four-step's outer pass, persistent and fed by TMA
+// (k_outer.cu): n = 2^log_r * 2^16, log_r = 5..8.
+struct OuterArgs {
+    CUtensorMap tm;      // the input chunk as [segments * R][2^16] complex64, box [4096 / R][R]
+    float2 *out;         // the workspace, unit by unit
+    const float2 *twL;   // stage tables of an R-point line
+    const float2 *tw4a;  // w_n^{(t mod 16) j}, [16][2^16]
+    const float2 *tw4b;  // w_n^{16 (t div 16) j}, [R / 16][2^16]
+    int *err;            // set when a tile's copy never completed
+    int64_t ntiles;      // segments * 2^16 / (4096 / R)
+};
+cudaError_t launch_outer(int log_r, int sign, const OuterArgs &a, cudaStream_t st);
 int pass_log_w(int log_l);
 
 // Single-pass cluster kernel for n = 2^log_n, 2^13..2^17; log_c selects the

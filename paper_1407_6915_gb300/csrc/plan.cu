@@ -618,35 +618,25 @@ int exec_fourstep_ilv(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg
 {
     const int log_r = p->ilv_log_r;
     const int64_t n = p->n, R = int64_t(1) << log_r, M = n >> log_r;
-    const int64_t W = outer_pass_columns(log_r);  // columns per outer tile
+    const int64_t W = int64_t(4096) >> log_r;  // columns per outer tile
     const fftseg_plan_s *q = p->inner;
     const int64_t n1 = 256, n2 = 256;
     for (int64_t s0 = 0; s0 < nseg; s0 += p->work_segs) {
         const int64_t cnt = nseg - s0 < p->work_segs ? nseg - s0 : p->work_segs;
-        LinesArgs A{};  // Y_t[j] = w_n^{j t} DFT_R over t' of x[j + M t'], stored unit by unit
-        A.in = static_cast<const float2 *>(d_in) + s0 * n;
-        A.out = p->work;
-        A.tiles_per_seg = M / W;
-        A.nseg = cnt;
-        A.in_seg = n;
-        A.out_seg = n;
-        A.in_tile = W;
-        A.out_tile = W * R;
-        A.in_cs = 1;
-        A.in_is = M;
-        A.out_cs = R;
-        A.out_is = 1;
-        A.twL = p->twA;
-        A.tw4a = p->tw4a;
-        A.tw4b = p->tw4b;
-        A.tw_ncols = M;
-        A.tw_log_k = 4;
-        A.out_ilv = 1;
-        A.ilv_n1 = n1;
-        A.ilv_n2 = n2;
-        A.ilv_blk = 32 * M;
-        A.scale = 1.f;
-        cudaError_t e = launch_outer_pass(log_r, p->direction, A, cnt * (M / W), st);
+        // Y_t[j] = w_n^{j t} DFT_R over t' of x[j + M t'], stored unit by unit
+        OuterArgs O{};
+        const int64_t dims[2] = {M, cnt * R};
+        const int64_t strides[1] = {M * 8};
+        const uint32_t box[2] = {(uint32_t)W, (uint32_t)R};
+        const int trc = encode_tmap(&O.tm, static_cast<const float2 *>(d_in) + s0 * n, 2, dims, strides, box, 8, 0);
+        if (trc != FFTSEG_OK) return trc;
+        O.out = p->work;
+        O.twL = p->twA;
+        O.tw4a = p->tw4a;
+        O.tw4b = p->tw4b;
+        O.err = p->d_err;
+        O.ntiles = cnt * (M / W);
+        cudaError_t e = launch_outer(log_r, p->direction, O, st);
         if (e != cudaSuccess) return cuda_error(e, "interleaved four-step: outer pass launch");
         count_launches(1);
         // units of 32 transforms: unit u = s G + b, transforms 32 b .. 32 b + 31 of segment s
