@@ -1072,8 +1072,13 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
 }
 
 // Real-signal plan: a complex plan of n/2 points (its schedule flags, and an
-// autotune request, go to it), the split/join twiddles w_n^k (k <= n/4) and an
-// intermediate of kRealChunkBytes that stays in L2 between the two passes.
+// autotune request, go to it), the split/join twiddles w_n^k (k <= n/4) and,
+// unless the split is fused, an intermediate of kRealSplitChunkBytes between
+// the two passes.  (Measured on GB300, 4 GiB of samples at n = 2^16..2^20:
+// 512 MiB chunks, 16 launches, 0.33-0.35 of the copy peak; 32 MiB chunks,
+// which stay in L2, 256 launches, 0.21-0.25.)  FFTSEG_REAL_CHUNK_MB, read at
+// plan creation, sets another size.  Frame plans keep chunks of
+// kRealChunkBytes.
 constexpr int64_t kRealChunkBytes = 32ll << 20;
 
 int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int precision, int out_kind,
@@ -1104,7 +1109,7 @@ int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int n
     else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
     const int64_t M = n / 2;
     p->log_n1 = ilog2(M);
-    int64_t cs = kRealChunkBytes / (M * 8);
+    int64_t cs = ((int64_t)env_int("FFTSEG_REAL_CHUNK_MB", 512, 1, 4096) << 20) / (M * 8);
     if (cs < 1) cs = 1;
     if (cs > batch) cs = batch;
     p->rchunk = cs;

@@ -33,6 +33,13 @@ def real_signal(seed, nseg, n):
     return siggen.tones(seed, nseg * n // 2).view(np.float32).reshape(nseg, n)
 
 
+@pytest.fixture(autouse=True)
+def small_chunks(monkeypatch):
+    # 32 MiB chunks of the n/2-point intermediate (the default is 512 MiB), so
+    # that modest batches span several chunks
+    monkeypatch.setenv("FFTSEG_REAL_CHUNK_MB", "32")
+
+
 def nseg_for(n):
     # more than one 32 MiB chunk of the n/2-point intermediate, plus a ragged tail
     return max(3, (48 << 20) // (4 * n) + 1) if n <= (1 << 20) else 3
@@ -148,3 +155,29 @@ def test_real_plan_rejections():
         plan.exec_ptr(buf.data_ptr(), buf.data_ptr())  # out of place only
     with pytest.raises(fs.FFTSegError):
         plan.exec_host(torch.zeros(2 << 12), torch.zeros(2 << 12))
+
+
+@pytest.mark.parametrize("direction", [FWD, INV])
+def test_default_chunks(monkeypatch, direction):
+    # the default 512 MiB chunks: 2^19-point segments (2 MiB of intermediate
+    # each), 300 of them span two chunks, the second one ragged
+    monkeypatch.delenv("FFTSEG_REAL_CHUNK_MB")
+    n, B = 1 << 19, 300
+    plan = fs.Plan(n, B, direction, fs.NORM_NONE if direction == FWD else fs.NORM_BACKWARD, flags=fs.FLAG_REAL)
+    info = plan.info()
+    assert info["work_segs"] == 256 and info["launches_per_exec"] == 4, info
+    x = real_signal(950 + direction, B, n)
+    sample = np.r_[0, 255, 256, B - 1]
+    if direction == FWD:
+        got = plan.exec(torch.from_numpy(x).cuda())
+        torch.cuda.synchronize()
+        plan.check()
+        ref = oracle.rfft(x[sample])
+        assert rel_l2(got.cpu().numpy()[sample], ref) <= tol_fp32(n)
+    else:
+        X = siggen.tones(960, B * (n // 2 + 1)).reshape(B, n // 2 + 1)  # any bins (imaginary parts of the real ones ignored)
+        got = plan.exec(torch.from_numpy(X).cuda())
+        torch.cuda.synchronize()
+        plan.check()
+        ref = oracle.irfft(X[sample], n, fs.NORM_BACKWARD)
+        assert rel_l2(got.cpu().numpy()[sample], ref) <= tol_fp32(n)
