@@ -465,10 +465,11 @@ def tc_split(peak):
 
 
 def real_bench(peak, sizes=None):
-    """Real-signal segments (FLAG_REAL), forward: 4 GiB of float32 samples cut
-    into n-point segments (n = 1024, the paper's record size, and 65536), to
-    the n/2 + 1 bins of each segment.  Algorithmic bytes per segment: 4n in,
-    8 (n/2 + 1) out.  `sizes`: other (n, segments) pairs (profiler captures)."""
+    """Real-signal segments (FLAG_REAL): 4 GiB of float32 samples cut into
+    n-point segments (n = 1024, the paper's record size, and 65536), to the
+    n/2 + 1 bins of each segment (forward) and back (inverse, timed on the
+    forward's bins).  Algorithmic bytes per segment: 4n and 8 (n/2 + 1).
+    `sizes`: other (n, segments) pairs (profiler captures)."""
     import torch
     import paper_1407_6915_gb300 as fs
     import siggen
@@ -490,17 +491,30 @@ def real_bench(peak, sizes=None):
         plan.check()
         ms = e0.elapsed_time(e1) / 5
         algo = B * (4.0 * n + 8.0 * (n // 2 + 1))
-        # round trip through the inverse real plan (1/n) against the samples
+        # round trip through the inverse real plan (1/n) against the samples,
+        # and the inverse plan's own time (the same bytes the other way)
         inv = fs.Plan(n, B, fs.INVERSE, fs.NORM_BACKWARD, flags=fs.FLAG_REAL)
         xr = inv.exec(y)
+        for _ in range(2):
+            inv.exec(y, out=xr)
+        e0.record()
+        for _ in range(5):
+            inv.exec(y, out=xr)
+        e1.record()
         torch.cuda.synchronize()
         inv.check()
+        inv_ms = e0.elapsed_time(e1) / 5
+        xr = inv.exec(y)
+        torch.cuda.synchronize()
         err = float(torch.linalg.vector_norm(xr - x) / torch.linalg.vector_norm(x))
         rows.append({"n": n, "segments": B, "ms": round(ms, 4),
                      "gflops_real_convention": round(2.5 * n * math.log2(n) * B / (ms / 1e3) / 1e9, 1),
                      "gbs_algorithmic": round(algo / (ms / 1e3) / 1e9, 1),
                      "hbm_frac": round(algo / (ms / 1e3) / 1e9 / peak, 4),
                      "launches_per_exec": plan.info()["launches_per_exec"],
+                     "inverse_ms": round(inv_ms, 4),
+                     "inverse_hbm_frac": round(algo / (inv_ms / 1e3) / 1e9 / peak, 4),
+                     "inverse_launches_per_exec": inv.info()["launches_per_exec"],
                      "round_trip_rel_l2": err})
         del x, y, h, plan, inv, xr
         torch.cuda.empty_cache()

@@ -1077,9 +1077,7 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
 // the two passes.  (Measured on GB300, 4 GiB of samples at n = 2^16..2^20:
 // 512 MiB chunks, 16 launches, 0.33-0.35 of the copy peak; 32 MiB chunks,
 // which stay in L2, 256 launches, 0.21-0.25.)  FFTSEG_REAL_CHUNK_MB, read at
-// plan creation, sets another size.  Frame plans keep chunks of
-// kRealChunkBytes.
-constexpr int64_t kRealChunkBytes = 32ll << 20;
+// plan creation, sets another size.
 
 int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int precision, int out_kind,
                 unsigned flags)
@@ -1165,7 +1163,11 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
     p->path = PATH_FRAMES;
     p->hop = hop;
     p->window = window;
-    int64_t cs = kRealChunkBytes / (n * 8);
+    // chunks of windowed frames, 512 MiB (FFTSEG_FRAMES_CHUNK_MB): measured on
+    // GB300 at n = 2^14..2^18 with hops that leave the lane-line kernel, 0.27-0.31
+    // of the copy peak against 0.17-0.23 in 32 MiB chunks (kept in L2, but 16x
+    // the launches of the inner plan)
+    int64_t cs = ((int64_t)env_int("FFTSEG_FRAMES_CHUNK_MB", 512, 1, 4096) << 20) / (n * 8);
     if (cs < 1) cs = 1;
     if (cs > batch) cs = batch;
     p->rchunk = cs;

@@ -26,6 +26,13 @@ def built():
     assert torch.cuda.is_available()
 
 
+@pytest.fixture(autouse=True)
+def small_chunks(monkeypatch):
+    # 32 MiB chunks of windowed frames (the default is 512 MiB), so that
+    # modest batches span several chunks
+    monkeypatch.setenv("FFTSEG_FRAMES_CHUNK_MB", "32")
+
+
 def signal(seed, samples):
     return siggen.tones(seed, samples)
 
