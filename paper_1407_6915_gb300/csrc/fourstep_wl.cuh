@@ -84,6 +84,9 @@ struct FourStepWlArgs {
     // t goes to X[t + R (k1 + N1 k2)] of segment s
     int ilv_r;
     int ilv_log_g;
+    // 1: the output is |X|^2, float32, in the same places (tmO over 4-byte
+    // elements, box [W_B][256], the W_B * 4-byte swizzle)
+    int out_power;
 };
 
 // One pass over lines of L = 2^LOG_L points in tiles of E = 2^LOG_E points.
@@ -296,7 +299,18 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                 const bool valid = kind == KIND_B;
                 const int rt = valid ? w : -w - 1;
                 if (lane == 0) {
-                    if (valid) {
+                    if (valid && a.out_power) {
+                        // one float box per 256 rows: [W_B floats][256 k2]
+                        constexpr int RBP = PB::W * 4;
+#pragma unroll
+                        for (int q = 0; q < PB::NBOXY; ++q)
+                            tma_store_3d_hint(&a.tmO,
+                                              ILV ? rt * a.ilv_r + (s & ((1 << a.ilv_log_g) - 1)) * 32 : rt * PB::W,
+                                              q * 256, ILV ? s >> a.ilv_log_g : s,
+                                              reinterpret_cast<char *>(P + b * E) + q * 256 * RBP, stream_policy);
+                        bulk_commit();
+                        bulk_wait_read();  // the store has read the buffer
+                    } else if (valid) {
 #pragma unroll
                         for (int p = 0; p < PB::NPANEL; ++p)
 #pragma unroll
@@ -537,18 +551,38 @@ __global__ void __launch_bounds__(FourStepWlShape<LOG_N1, LOG_N2, LOG_E, NB, MIN
                                float2{}, a.err);
             else
                 wl_line<PS, S>(v, Pc, tb, c, j, group, TWB, nullptr, nullptr, float2{}, a.err);
-            const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
-            const uint32_t rb = tb + (uint32_t)((c / PS::PW) * PS::PANEL_BYTES) + (uint32_t)(PS::ROWB * j) +
-                                (uint32_t)(16 * (ch ^ ((j7 >> PS::SWZ_S) & PS::SWZ_M)) + 8 * h);
-            wl_group_sync<PS::GROUP>(group);  // every lane of the line has read its exchange rows
+            if (a.out_power) {
+                // |X|^2 staged as the float output box: row k2 holds the tile's
+                // W_B lines in RBP = 4 W_B bytes, 16-byte chunks swizzled by the
+                // row like the complex panels.  Rows span every line's column, so
+                // all compute warps must have read their exchange rows first.
+                constexpr int RBP = PS::W * 4, SP = RBP == 128 ? 0 : RBP == 64 ? 1 : 2, MP = RBP / 16 - 1;
+                static_assert(RBP >= 32 && RBP <= 128, "float output rows of 32..128 bytes");
+                asm volatile("bar.sync 15, %0;" ::"n"(TC) : "memory");
 #pragma unroll
-            for (int e = 0; e < PS::Q; ++e)
+                for (int e = 0; e < PS::Q; ++e)
 #pragma unroll
-                for (int r = 0; r < PS::P; ++r) {
-                    const uint32_t off = rb + PS::ROWB * (PS::P * e + 32 * r);
-                    if (FFTSEG_CHECK(off - tb < Sh::TILE_BYTES, a.err))
-                        *reinterpret_cast<float2 *>(Pc + off) = v[e * PS::P + r];
-                }
+                    for (int r = 0; r < PS::P; ++r) {
+                        const int k2 = j + PS::P * e + 32 * r;
+                        const uint32_t off = tb + (uint32_t)(k2 * RBP) +
+                                             (uint32_t)((((c >> 2) ^ ((k2 >> SP) & MP)) << 4) + (c & 3) * 4);
+                        if (FFTSEG_CHECK(off - tb < Sh::TILE_BYTES, a.err))
+                            *reinterpret_cast<float *>(Pc + off) = power_of(v[e * PS::P + r]);
+                    }
+            } else {
+                const int j7 = j & 7, ch = (c % PS::PW) >> 1, h = c & 1;
+                const uint32_t rb = tb + (uint32_t)((c / PS::PW) * PS::PANEL_BYTES) + (uint32_t)(PS::ROWB * j) +
+                                    (uint32_t)(16 * (ch ^ ((j7 >> PS::SWZ_S) & PS::SWZ_M)) + 8 * h);
+                wl_group_sync<PS::GROUP>(group);  // every lane of the line has read its exchange rows
+#pragma unroll
+                for (int e = 0; e < PS::Q; ++e)
+#pragma unroll
+                    for (int r = 0; r < PS::P; ++r) {
+                        const uint32_t off = rb + PS::ROWB * (PS::P * e + 32 * r);
+                        if (FFTSEG_CHECK(off - tb < Sh::TILE_BYTES, a.err))
+                            *reinterpret_cast<float2 *>(Pc + off) = v[e * PS::P + r];
+                    }
+            }
             fence_proxy_async();  // read by the retirer's TMA store
         }
         __syncwarp();

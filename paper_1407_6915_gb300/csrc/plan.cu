@@ -34,7 +34,7 @@ bool is_pow2(int64_t n) { return n >= 1 && (n & (n - 1)) == 0; }
 // producer or CTA-tile kernels: the lane-local-line kernels can run it.
 bool lane_kernels_apply(const fftseg_plan_s *p)
 {
-    return p->precision == FFTSEG_PREC_FP32 && p->out_kind == FFTSEG_OUT_COMPLEX &&
+    return p->precision == FFTSEG_PREC_FP32 &&
            !(p->flags & (FFTSEG_FLAG_FOURSTEP_PRODUCER | FFTSEG_FLAG_FOURSTEP_TILES));
 }
 // n = 2^16..2^20: the lane-line kernel (fourstep_wl.cuh), measured faster
@@ -54,7 +54,8 @@ bool uses_fourstep_ilv(const fftseg_plan_s *p)
 // n = 256 x 256 on request: the warp-line kernel (fourstep_hw.cuh).
 bool uses_fourstep_hw(const fftseg_plan_s *p)
 {
-    return p->log_n == 16 && lane_kernels_apply(p) && (p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
+    return p->log_n == 16 && lane_kernels_apply(p) && p->out_kind == FFTSEG_OUT_COMPLEX &&
+           (p->flags & FFTSEG_FLAG_FOURSTEP_WARP_LINES);
 }
 // Bluestein plans whose M-point rows fit one block tile (M <= 4096, the
 // inner forward plan on the block path) run as one fused kernel.
@@ -415,18 +416,17 @@ int build_fp32(fftseg_plan p)
     }
     int l1, l2, lc;
     const int want_c = (int)((p->flags >> 8) & 0xFu);
-    // measured on GB300: the cluster path wins up to 2^15 (and for |X|^2
-    // output at 2^16), the persistent four-step above: at 2^16 its lane-line
-    // kernel (16384 segments: 4.14 ms against 5.5 ms for 16-CTA clusters,
-    // whose all-to-all exchange is bound by the SM-to-SM network), from 2^17
-    // on because a 16-CTA cluster per segment leaves SMs idle
+    // measured on GB300: the cluster path wins up to 2^15, the persistent
+    // four-step above: at 2^16 its lane-line kernel (16384 segments: 4.14 ms
+    // against 5.5 ms for 16-CTA clusters, whose all-to-all exchange is bound
+    // by the SM-to-SM network; |X|^2 of 4 GiB: 1.97 ms against 2.75 ms), from
+    // 2^17 on because a 16-CTA cluster per segment leaves SMs idle
     // (at 2^24 with complex output the two-pass path measured 8 % faster than
     // the persistent four-step: a segment's 128 MiB intermediate cannot stay
     // in L2, so both make two HBM passes)
     // (complex FP32 output at 2^21..2^24 runs the interleaved four-step instead)
     const bool twopass_24 = ln == 24 && p->out_kind == FFTSEG_OUT_COMPLEX && !uses_fourstep_ilv(p);
-    if (!force2 && want_c == 0 && !twopass_24 && (ln >= 17 || (ln == 16 && p->out_kind == FFTSEG_OUT_COMPLEX)))
-        return build_fourstep(p);
+    if (!force2 && want_c == 0 && !twopass_24 && ln >= 16) return build_fourstep(p);
     if (!force2 && ln >= 13 && ln <= 17 && !cluster_shape(ln, want_c, &l1, &l2, &lc))
         return set_error(FFTSEG_E_UNSUPPORTED, "plan_create: no cluster of 2^%d CTAs is built for n=2^%d",
                          want_c, ln);
@@ -586,9 +586,14 @@ int exec_fourstep_wl(fftseg_plan p, const void *in, void *d_out, int64_t nseg, c
         const uint32_t box[4] = {(uint32_t)pwb, 256, 1, 1};
         rc = encode_tmap(&a.tmB, p->ring, 4, dims, strides, box, 8, (int)(pwb * 8));
     }
-    if (rc == FFTSEG_OK)
-        rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8, (int)(pwb * 8));
+    if (rc == FFTSEG_OK) {
+        if (p->out_kind == FFTSEG_OUT_POWER)  // |X|^2: float rows of the row tile's wb lines
+            rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 4, n * 4, (uint32_t)wb, 256, 4, (int)(wb * 4));
+        else
+            rc = encode_tmap_3d_swz(&a.tmO, d_out, n1, n2, nseg, n1 * 8, n * 8, (uint32_t)pwb, 256, 8, (int)(pwb * 8));
+    }
     if (rc != FFTSEG_OK) return rc;
+    a.out_power = p->out_kind == FFTSEG_OUT_POWER;
     const int64_t nc = (nseg + cs - 1) / cs;
     if (nc * cs * ((n2 / wa) + (n1 / wb)) >= (int64_t(1) << 31))
         return set_error(FFTSEG_E_INVALID, "exec: too many tiles for one launch of the lane-line kernel");
@@ -653,10 +658,17 @@ int exec_fourstep_ilv(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg
             const uint32_t box[4] = {16, 256, 1, 1};
             rc = encode_tmap(&a.tmB, q->ring, 4, dims, strides, box, 8, 128);
         }
-        if (rc == FFTSEG_OK)  // X[t + R (k1 + N1 k2)] as [segment][k2][R k1 + t]
-            rc = encode_tmap_3d_swz(&a.tmO, static_cast<float2 *>(d_out) + s0 * n, n1 * R, n2, cnt, n1 * R * 8,
-                                    n * 8, 16, 256, 8, 128);
+        const bool power = p->out_kind == FFTSEG_OUT_POWER;
+        if (rc == FFTSEG_OK) {  // X[t + R (k1 + N1 k2)] as [segment][k2][R k1 + t]
+            if (power)
+                rc = encode_tmap_3d_swz(&a.tmO, static_cast<float *>(d_out) + s0 * n, n1 * R, n2, cnt, n1 * R * 4,
+                                        n * 4, 32, 256, 4, 128);
+            else
+                rc = encode_tmap_3d_swz(&a.tmO, static_cast<float2 *>(d_out) + s0 * n, n1 * R, n2, cnt, n1 * R * 8,
+                                        n * 8, 16, 256, 8, 128);
+        }
         if (rc != FFTSEG_OK) return rc;
+        a.out_power = power;
         const int64_t nc = (units + cs - 1) / cs;
         a.ring = q->ring;
         a.twA = q->twA;

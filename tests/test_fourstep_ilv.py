@@ -94,3 +94,21 @@ def test_interleaved_fourstep_impulses():
     for s, j0 in enumerate(j0s):
         ref = np.exp(-2j * np.pi * ((j0 * k) % n) / n)
         assert rel_l2(got[s], ref) <= tol_fp32(n), j0
+
+
+@pytest.mark.parametrize("log_n,B", [(21, 35), (24, 5)])
+def test_interleaved_fourstep_power(log_n, B):
+    # |X|^2 at X[t + R k]: the row pass's float boxes of 32 transforms
+    n = 1 << log_n
+    x = siggen.tones(1780 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD, fs.NORM_ORTHO, out_kind=fs.OUT_POWER)
+    assert plan.info()["n1"] == n >> 16, plan.info()
+    buf, y = guard(torch.empty(B, n, dtype=torch.float32, device="cuda"))
+    plan.exec(torch.from_numpy(x).cuda(), out=y)
+    torch.cuda.synchronize()
+    plan.check()
+    check_guard(buf)
+    chunk = plan.info()["work_segs"]
+    sample = np.unique(np.r_[0, chunk - 1, chunk, B - 1])
+    X = oracle.fft(x[sample], FWD, fs.NORM_ORTHO)
+    assert rel_l2(y.cpu().numpy()[sample], X.real ** 2 + X.imag ** 2) <= 2 * tol_fp32(n)

@@ -57,6 +57,25 @@ def test_lane_line_fourstep_matches_oracle(log_n, B, direction, norm):
     np.testing.assert_array_equal(d.cpu().numpy(), got)
 
 
+# |X|^2 from the row pass: the float output box of each row tile (W_B = 32,
+# 16 or 8 lines: 128-, 64- and 32-byte rows), several ring chunks, every
+# segment compared, nothing written past the output
+@pytest.mark.parametrize("log_n,B", [(16, 293), (17, 139), (18, 69), (19, 35), (20, 17)])
+@pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_ORTHO])
+def test_lane_line_fourstep_power(log_n, B, norm):
+    n = 1 << log_n
+    x = siggen.tones(1650 + log_n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, FWD, norm, out_kind=fs.OUT_POWER, flags=fs.FLAG_FOURSTEP_L2)
+    assert plan.info()["path"] == "four-step" and plan.info()["launches_per_exec"] == 1
+    buf, y = guard(torch.empty(B, n, dtype=torch.float32, device="cuda"))
+    plan.exec(torch.from_numpy(x).cuda(), out=y)
+    torch.cuda.synchronize()
+    plan.check()
+    check_guard(buf)
+    X = oracle.fft(x, FWD, norm)
+    assert rel_l2(y.cpu().numpy(), X.real ** 2 + X.imag ** 2) <= 2 * tol_fp32(n)
+
+
 def test_lane_line_fourstep_round_trip_and_partial_batches():
     n, B = 1 << 18, 21
     x = siggen.uniform(1650, B * n).reshape(B, n)
