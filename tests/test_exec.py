@@ -235,3 +235,21 @@ def test_launch_counter_counts_kernels():
     before = fs.launch_count()
     plan.exec(x)
     assert fs.launch_count() - before == plan.info()["launches_per_exec"]
+
+
+def test_default_schedules():
+    # the plan picks these schedules by default (the measured best on GB300):
+    # (n, output) -> (path, n1, n2, launches per exec of one segment)
+    P = fs.OUT_POWER
+    expect = {
+        (1 << 4, 0): ("block", 16, 1, 1), (1 << 12, 0): ("block", 4096, 1, 1),
+        (1 << 13, 0): ("cluster", 64, 128, 1), (1 << 15, 0): ("cluster", 256, 128, 1),
+        (1 << 16, 0): ("four-step", 256, 256, 1), (1 << 16, P): ("four-step", 256, 256, 1),
+        (1 << 20, 0): ("four-step", 1024, 1024, 1), (1 << 20, P): ("four-step", 1024, 1024, 1),
+        (1 << 21, 0): ("four-step", 32, 65536, 2), (1 << 24, 0): ("four-step", 256, 65536, 2),
+        (1 << 24, P): ("four-step", 256, 65536, 2), (1000, 0): ("mixed-radix", 1000, 1, 1),
+    }
+    for (n, kind), (path, n1, n2, launches) in expect.items():
+        plan = fs.Plan(n, 1, FWD, out_kind=P if kind else fs.OUT_COMPLEX)
+        info = plan.info()
+        assert (info["path"], info["n1"], info["n2"], info["launches_per_exec"]) == (path, n1, n2, launches), (n, kind, info)
