@@ -464,7 +464,14 @@ FDEV void rf_place(int k1, int &d, int &c)
     c = hb * H + (m & (H - 1));
 }
 
-template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false>
+// RI (inverse real-signal segments, S = +1): the input is the n + 1 bins
+// X[0..n] of each segment's real DFT (stride n + 1), and the column pass
+// reads them straight from global memory, each point m taking
+//   Z[m] = (A + B) + i conj(w_{2n}^m) (A - B),  A = X[m], B = conj(X[n - m])
+// (the imaginary parts of X[0] and X[n] ignored), so that the inverse
+// n-point transform of Z gives x[2j] + i x[2j + 1] (no slab copy, no
+// intermediate; the mirror point's load is another CTA's, mostly from L2).
+template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false, bool RI = false>
 __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, ClusterShape<LOG_N1, LOG_N2, LOG_C>::MINB)
     k_cluster(const __grid_constant__ ClusterArgs a)
 {
@@ -544,16 +551,37 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
 
     const int64_t cid = blockIdx.x >> LOG_C, ncl = gridDim.x >> LOG_C;
     int64_t s = cid;
-    if (s < a.nseg && tid == 0) issue(s);
+    if (!RI && s < a.nseg && tid == 0) issue(s);
     const float scale = a.scale;
     cluster_arrive_relaxed();  // X is free
     for (int k = 0; s < a.nseg; s += ncl, ++k) {
         if (tid == 0) mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
-        mbar_wait(bar, k & 1, a.err);
+        if constexpr (!RI) mbar_wait(bar, k & 1, a.err);
         float2 v[16];
 
         // column pass: line c is column j2 = rank*WA + c, points j1 = i
-        gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return U[i * WA + c]; });
+        if constexpr (RI) {
+            static_assert(!RI || (S == 1 && !RF), "real-signal bins in: inverse only");
+            const float2 *Xs = a.in + s * (N + 1);
+            gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) {
+                const int m = i * N2 + rank * WA + c;
+                float2 A = __ldg(Xs + m), Cm = __ldg(Xs + ((int)N - m));  // X[m], X[n - m] (X[n] at m = 0)
+                if (m == 0) {
+                    A.y = 0.f;
+                    Cm.y = 0.f;
+                }
+                // conj(w_{2n}^m) from the table of m <= n/2 (w_{2n}^m = -conj(w_{2n}^{n-m}) above)
+                const bool lo = 2 * m <= (int)N;
+                const float2 t = __ldg(a.rtw + (lo ? m : (int)N - m));
+                const float2 cw = lo ? make_float2(t.x, -t.y) : make_float2(-t.x, -t.y);
+                const float sx = A.x + Cm.x, sy = A.y - Cm.y;  // A + B, B = conj(X[n - m])
+                const float dx = A.x - Cm.x, dy = A.y + Cm.y;  // A - B
+                const float ex = cw.x * dx - cw.y * dy, ey = cw.x * dy + cw.y * dx;
+                return make_float2(sx - ey, sy + ex);  // (A + B) + i conj(w) (A - B)
+            });
+        } else {
+            gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return U[i * WA + c]; });
+        }
         run_stages<LOG_N1, Sh::LOG_WA, true, S, T, Sh::PSA, 0, true, false, PREC_FP32, false, true>(v, U, TWA);
         __syncthreads();  // U no longer read as column-pass scratch
 
@@ -581,7 +609,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
         mbar_wait(rbar, k & 1, a.err);  // every slice of this CTA's rows has arrived
         if (tid == 0) {
             bulk_wait_read_all();  // the outgoing copies have read U: refill it
-            if (s + ncl < a.nseg) issue(s + ncl);
+            if (!RI && s + ncl < a.nseg) issue(s + ncl);
         }
 
         // row pass: line c is row k1 = rank*WB + c, points j2 = i

@@ -48,6 +48,10 @@ cudaError_t launch_cluster(int log_n, int log_c, int sign, const ClusterArgs &a,
 // Forward real-signal segments of 2^(log_n + 1) samples on the cluster kernel
 // (the split into the real DFT's bins in its epilogue; a.rtw, a.out_power, a.scale).
 cudaError_t launch_cluster_r2c(int log_n, int log_c, const ClusterArgs &a, cudaStream_t st);
+// Inverse real-signal segments (n = 2^13, 2^14): the n + 1 bins in (a.in,
+// stride n + 1), the 2n samples out (a.out), the join fused into the column
+// pass's loads.
+cudaError_t launch_cluster_c2r(int log_n, int log_c, const ClusterArgs &a, cudaStream_t st);
 // Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
 bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
 

@@ -73,11 +73,16 @@ bool frames_fused(const fftseg_plan_s *p)
 
 // Forward real-signal plans whose n/2-point complex transform runs on the
 // block or the cluster kernel split the spectrum inside that kernel (one
-// pass, no intermediate).
+// pass, no intermediate); inverse ones join the bins inside the cluster
+// kernel up to n/2 = 2^14.  (The fused join reads its bins with plain loads,
+// a point and its mirror, no prefetch: measured on GB300 at n = 2^14, 2^15,
+// 2^16, 2^17 and 2^18: 0.37, 0.35, 0.29, 0.25, 0.22 of the copy peak, against
+// 0.34-0.35 chunked from n = 2^16 on.)
 bool real_fused(const fftseg_plan_s *p)
 {
-    return p->path == PATH_REAL && p->direction == FFTSEG_FORWARD && p->inner &&
-           (p->inner->path == PATH_BLOCK || p->inner->path == PATH_CLUSTER);
+    if (p->path != PATH_REAL || !p->inner) return false;
+    if (p->direction == FFTSEG_INVERSE) return p->inner->path == PATH_CLUSTER && p->inner->log_n <= 14;
+    return p->inner->path == PATH_BLOCK || p->inner->path == PATH_CLUSTER;
 }
 int ilog2(int64_t n)
 {
@@ -837,6 +842,24 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             count_launches(1);
             return FFTSEG_OK;
         }
+        if (real_fused(p) && p->direction == FFTSEG_INVERSE) {
+            // n/2 = 2^13..2^17 on the cluster kernel: the join in its column pass's loads
+            const fftseg_plan_s *q = p->inner;
+            ClusterArgs a{};
+            a.in = static_cast<const float2 *>(d_in);
+            a.out = d_out;
+            a.nseg = nseg;
+            a.err = p->d_err;
+            a.twA = q->twA;
+            a.twB = q->twB;
+            a.tw4 = q->tw4a;
+            a.rtw = p->rtw;
+            a.scale = p->scale;
+            cudaError_t e = launch_cluster_c2r(q->log_n, q->log_c, a, st);
+            if (e != cudaSuccess) return cuda_error(e, "real-signal cluster kernel launch");
+            count_launches(1);
+            return FFTSEG_OK;
+        }
         if (real_fused(p)) {
             // n/2 = 2^13..2^17 on the cluster kernel: the split in its epilogue
             const fftseg_plan_s *q = p->inner;
@@ -1124,11 +1147,10 @@ int create_real(fftseg_plan *out, int64_t n, int64_t batch, int direction, int n
     if (cs > batch) cs = batch;
     p->rchunk = cs;
     unsigned iflags = flags & ~FFTSEG_FLAG_REAL;
-    // forward plans of 2^17 and 2^18 samples: the cluster kernel with the
-    // split in its epilogue (one pass) measured 1.7x and 1.2x faster than
-    // the chunked lane-line transform plus a split pass
-    if (direction == FFTSEG_FORWARD && (M == (1 << 16) || M == (1 << 17)) &&
-        !(flags & (kPathFlags | FFTSEG_FLAG_AUTOTUNE)))
+    // forward plans of 2^17 samples: the cluster kernel with the split in its
+    // epilogue (one pass) measured 0.39 of the copy peak against 0.36 for the
+    // chunked lane-line transform plus a split pass (at 2^18: 0.28 against 0.35)
+    if (direction == FFTSEG_FORWARD && M == (1 << 16) && !(flags & (kPathFlags | FFTSEG_FLAG_AUTOTUNE)))
         iflags |= FFTSEG_FLAG_CLUSTER_LOG2(4);
     int rc = fftseg_plan_create(&p->inner, M, cs, direction, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
                                 FFTSEG_OUT_COMPLEX, iflags);

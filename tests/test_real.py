@@ -111,6 +111,31 @@ def test_r2c_cluster_split(log_n, cflag, out_kind, norm):
             assert np.all(g[:, 0].imag == 0) and np.all(g[:, n // 2].imag == 0)
 
 
+# inverse plans whose n/2-point transform runs on the cluster kernel (up to
+# n/2 = 2^14) join the bins in its column pass (each point also reads its
+# mirror bin X[n/2 - m]): batches smaller than the grid and ragged, every
+# segment
+@pytest.mark.parametrize("log_n,cflag", [(14, 0), (15, 0)])
+@pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_BACKWARD, fs.NORM_ORTHO])
+def test_c2r_cluster_join(log_n, cflag, norm):
+    n = 1 << log_n
+    B = 37
+    X = siggen.tones(980 + log_n + cflag, B * (n // 2 + 1)).reshape(B, n // 2 + 1)
+    flags = fs.FLAG_REAL | (fs.FLAG_CLUSTER_LOG2(cflag) if cflag else 0)
+    plan = fs.Plan(n, B, INV, norm, flags=flags)
+    info = plan.info()
+    assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0, info
+    ref = oracle.irfft(X, n, norm)
+    d = torch.from_numpy(X).cuda()
+    for nseg in (B, 1, 5):
+        buf, got = guard(torch.empty(nseg, n, dtype=torch.float32, device="cuda"))
+        plan.exec(d, out=got, nseg=nseg)
+        torch.cuda.synchronize()
+        plan.check()
+        check_guard(buf)
+        assert rel_l2(got.cpu().numpy(), ref[:nseg]) <= tol_fp32(n), (nseg, rel_l2(got.cpu().numpy(), ref[:nseg]))
+
+
 @pytest.mark.parametrize("log_n", [2, 3, 6, 12, 13, 16, 20])
 @pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_BACKWARD, fs.NORM_ORTHO])
 def test_c2r_matches_oracle(log_n, norm):
