@@ -192,12 +192,16 @@ FDEV void wl_line(float2 (&v)[32], char *Pc, uint32_t tb, int c, int j, int grou
 #pragma unroll
     for (int r = 0; r < 32; ++r) v[r] = at(rb + ROWB * P * r);
     if (wrow) {  // the frame's window on rows j + P r of this column
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const float2 rr = __ldg(wrow + j + P * r);
+        // row factor of row j + P r: (cos, sin)(2 pi j / N1) times exp(2 pi i r / 32)
+        // (P r / N1 = r / 32), an exact constant rotation: one table entry per lane
+        const float2 r0 = __ldg(wrow + j);
+        unroll_for<32>([&](auto rc) {
+            constexpr int r = decltype(rc)::value;
+            float2 rr = rot32<r & 15, 1>(r0);
+            if constexpr (r >= 16) rr = make_float2(-rr.x, -rr.y);  // exp(i pi) = -1
             const float wv = 0.5f - 0.5f * (rr.x * wcol.x - rr.y * wcol.y);
             v[r] = make_float2(v[r].x * wv, v[r].y * wv);
-        }
+        });
     }
     dft32<S>(v);
     wl_group_sync<PS::GROUP>(group);  // every lane of the line has read its rows
