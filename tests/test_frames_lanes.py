@@ -73,3 +73,32 @@ def test_other_hops_keep_the_chunked_form():
     sample = np.r_[0, F // 2, F - 1]
     ref = np.concatenate([oracle.frames_fft(x[f * hop:], n, hop, 1, fs.WINDOW_HANN) for f in sample])
     assert rel_l2(got[sample].astype(np.complex128), ref) <= tol_fp32(n)
+
+
+@pytest.mark.parametrize("log_n,hop_rows,F", [(16, 128, 77), (20, 768, 13)])
+def test_fused_lane_frames_power(log_n, hop_rows, F):
+    # |X|^2 of windowed frames in the same single launch (the row pass's
+    # float output boxes)
+    n = 1 << log_n
+    hop = hop_rows * (1 << (log_n // 2))
+    x = siggen.tones(1970 + log_n, (F - 1) * hop + n)
+    plan = fs.FramePlan(n, hop, F, fs.WINDOW_HANN, fs.NORM_ORTHO, out_kind=fs.OUT_POWER)
+    info = plan.info()
+    assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0, info
+    got = plan.exec(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    plan.check()
+    X = oracle.frames_fft(x, n, hop, F, fs.WINDOW_HANN, fs.NORM_ORTHO)
+    assert rel_l2(got.cpu().numpy(), X.real ** 2 + X.imag ** 2) <= 2 * tol_fp32(n)
+
+
+def test_frames_above_2p20_run_chunked_on_the_interleaved_plan():
+    # 2^21-point frames: chunks of windowed frames through the interleaved
+    # four-step
+    n, hop, F = 1 << 21, 1 << 20, 5
+    x = siggen.tones(1980, (F - 1) * hop + n)
+    plan = fs.FramePlan(n, hop, F, fs.WINDOW_HANN)
+    got = run(plan, x, F, n)
+    sample = np.r_[0, F - 1]
+    ref = np.concatenate([oracle.frames_fft(x[f * hop:], n, hop, 1, fs.WINDOW_HANN) for f in sample])
+    assert rel_l2(got[sample].astype(np.complex128), ref) <= tol_fp32(n)
