@@ -636,13 +636,14 @@ def bluestein_bench(peak):
     """Lengths that are not powers of two, 2^29 complex64 samples (4 GiB)
     each, forward: n = 1000 and 3000 on the mixed-radix path (the default for
     lengths 2^a 3^b 5^c 7^d <= 4096), n = 1000 through Bluestein (M = 2048)
-    for comparison, and the prime 10007 through Bluestein (M = 32768).
-    Algorithmic bytes: 16 per point, as for every length."""
+    for comparison, and the primes 10007 and 40009 through Bluestein
+    (M = 32768 and 131072).  Algorithmic bytes: 16 per point, as for every
+    length."""
     import torch
     import paper_1407_6915_gb300 as fs
     import siggen
     rows = []
-    for n, flags in ((1000, 0), (3000, 0), (1000, fs.FLAG_BLUESTEIN), (10007, 0)):
+    for n, flags in ((1000, 0), (3000, 0), (1000, fs.FLAG_BLUESTEIN), (10007, 0), (40009, 0)):
         B = (1 << 29) // n
         x = torch.from_numpy(siggen.uniform(9, B * n)).cuda().view(B, n)
         plan = fs.Plan(n, B, fs.FORWARD, flags=flags)

@@ -6,11 +6,12 @@ namespace fftseg {
 
 namespace {
 
-template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false, bool RI = false>
+template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false, bool RI = false, bool BL = false,
+          bool BF = false>
 cudaError_t cluster_t(const ClusterArgs &a, cudaStream_t st)
 {
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
-    auto k = k_cluster<LOG_N1, LOG_N2, LOG_C, S, RF, RI>;
+    auto k = k_cluster<LOG_N1, LOG_N2, LOG_C, S, RF, RI, BL, BF>;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -107,6 +108,36 @@ cudaError_t launch_cluster_c2r(int log_n, int log_c, const ClusterArgs &a, cudaS
         // (n/2 = 2^13 and 2^14: larger inverse plans are faster chunked)
         case 13: return cluster_t<6, 7, 1, 1, false, true>(a, st);
         case 14: return cluster_t<7, 7, 2, 1, false, true>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cluster_blue_inv(int log_m, int log_c, const ClusterArgs &a, cudaStream_t st)
+{
+    int l1, l2, lc;
+    if (!cluster_shape(log_m, log_c, &l1, &l2, &lc)) return cudaErrorInvalidValue;
+    switch (log_m) {
+        case 13: return cluster_t<6, 7, 1, 1, false, false, true>(a, st);
+        case 14: return cluster_t<7, 7, 2, 1, false, false, true>(a, st);
+        case 15: return cluster_t<8, 7, 3, 1, false, false, true>(a, st);
+        case 16: return lc == 4 ? cluster_t<8, 8, 4, 1, false, false, true>(a, st)
+                                : cluster_t<8, 8, 3, 1, false, false, true>(a, st);
+        case 17: return cluster_t<8, 9, 4, 1, false, false, true>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_cluster_blue_fwd(int log_m, int log_c, const ClusterArgs &a, cudaStream_t st)
+{
+    int l1, l2, lc;
+    if (!cluster_shape(log_m, log_c, &l1, &l2, &lc)) return cudaErrorInvalidValue;
+    switch (log_m) {
+        case 13: return cluster_t<6, 7, 1, -1, false, false, false, true>(a, st);
+        case 14: return cluster_t<7, 7, 2, -1, false, false, false, true>(a, st);
+        case 15: return cluster_t<8, 7, 3, -1, false, false, false, true>(a, st);
+        case 16: return lc == 4 ? cluster_t<8, 8, 4, -1, false, false, false, true>(a, st)
+                                : cluster_t<8, 8, 3, -1, false, false, false, true>(a, st);
+        case 17: return cluster_t<8, 9, 4, -1, false, false, false, true>(a, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -376,6 +376,15 @@ struct ClusterArgs {
     const float2 *twB;  // stage twiddle tables, length N2
     const float2 *tw4;  // w_n^{k1 j2}, [N1][N2]
     const float2 *rtw;  // real-signal segments: w_{2n}^k for k = 0 .. n/2
+    // Bluestein rows (BL kernels, the inverse M-point transform of a row of
+    // n < M): the input times bl_bhat[m] as it is read; bin k < bl_n of the
+    // result times scale * bl_w[k] to out[row * bl_n + k]; bins k >= bl_n dropped.
+    // (BF kernels, the forward transform: point m of row s is
+    // in[s * bl_n + m] * bl_w[m] for m < bl_n and 0 above, read straight from
+    // global memory.)
+    const float2 *bl_bhat;
+    const float2 *bl_w;
+    int64_t bl_n;
     int *err;
     int out_power;
     float scale;
@@ -471,10 +480,18 @@ FDEV void rf_place(int k1, int &d, int &c)
 // (the imaginary parts of X[0] and X[n] ignored), so that the inverse
 // n-point transform of Z gives x[2j] + i x[2j + 1] (no slab copy, no
 // intermediate; the mirror point's load is another CTA's, mostly from L2).
-template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false, bool RI = false>
+// BL (Bluestein rows, S = +1): the inverse transform of the product with
+// B, its input multiplied by B as the column pass reads the slab, and the
+// chirp-out and the crop to n bins in the row pass's epilogue (the pointwise
+// product and chirp-out passes of the chunked form folded in).
+// BF (Bluestein rows, S = -1): the forward transform of the chirped row,
+// read from the n input samples directly (zero past n, no slab copy).
+template <int LOG_N1, int LOG_N2, int LOG_C, int S, bool RF = false, bool RI = false, bool BL = false,
+          bool BF = false>
 __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, ClusterShape<LOG_N1, LOG_N2, LOG_C>::MINB)
     k_cluster(const __grid_constant__ ClusterArgs a)
 {
+    constexpr bool DIRECT = RI || BF;  // the column pass reads global memory itself (no slab copy)
     using Sh = ClusterShape<LOG_N1, LOG_N2, LOG_C>;
     constexpr int N1 = 1 << LOG_N1, N2 = 1 << LOG_N2, T = Sh::T, E = Sh::E, C = Sh::C;
     constexpr int WA = 1 << Sh::LOG_WA, WB = 1 << Sh::LOG_WB;
@@ -551,12 +568,12 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
 
     const int64_t cid = blockIdx.x >> LOG_C, ncl = gridDim.x >> LOG_C;
     int64_t s = cid;
-    if (!RI && s < a.nseg && tid == 0) issue(s);
+    if (!DIRECT && s < a.nseg && tid == 0) issue(s);
     const float scale = a.scale;
     cluster_arrive_relaxed();  // X is free
     for (int k = 0; s < a.nseg; s += ncl, ++k) {
         if (tid == 0) mbar_expect_tx(rbar, (uint32_t)(C * Sh::SLICE * sizeof(float2)));  // this segment's rows
-        if constexpr (!RI) mbar_wait(bar, k & 1, a.err);
+        if constexpr (!DIRECT) mbar_wait(bar, k & 1, a.err);
         float2 v[16];
 
         // column pass: line c is column j2 = rank*WA + c, points j1 = i
@@ -578,6 +595,22 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
                 const float dx = A.x - Cm.x, dy = A.y + Cm.y;  // A - B
                 const float ex = cw.x * dx - cw.y * dy, ey = cw.x * dy + cw.y * dx;
                 return make_float2(sx - ey, sy + ex);  // (A + B) + i conj(w) (A - B)
+            });
+        } else if constexpr (BF) {
+            static_assert(!BF || (S == -1 && !RF && !BL), "Bluestein rows in: the forward transform only");
+            const int64_t nb = a.bl_n;
+            const float2 *xs = a.in + s * nb;
+            gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) {
+                const int64_t m = (int64_t)i * N2 + rank * WA + c;
+                if (m >= nb) return make_float2(0.f, 0.f);
+                const float2 x = __ldg(xs + m), w = __ldg(a.bl_w + m);
+                return make_float2(x.x * w.x - x.y * w.y, x.x * w.y + x.y * w.x);
+            });
+        } else if constexpr (BL) {
+            static_assert(!BL || (S == 1 && !RF && !RI), "Bluestein rows: the inverse transform only");
+            gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) {
+                const float2 x = U[i * WA + c], b = __ldg(a.bl_bhat + i * N2 + rank * WA + c);
+                return make_float2(x.x * b.x - x.y * b.y, x.x * b.y + x.y * b.x);
             });
         } else {
             gather<LOG_N1, Sh::LOG_WA, true, T, 0>(v, [&](int c, int i) { return U[i * WA + c]; });
@@ -609,7 +642,7 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
         mbar_wait(rbar, k & 1, a.err);  // every slice of this CTA's rows has arrived
         if (tid == 0) {
             bulk_wait_read_all();  // the outgoing copies have read U: refill it
-            if (!RI && s + ncl < a.nseg) issue(s + ncl);
+            if (!DIRECT && s + ncl < a.nseg) issue(s + ncl);
         }
 
         // row pass: line c is row k1 = rank*WB + c, points j2 = i
@@ -617,7 +650,18 @@ __global__ void __launch_bounds__(ClusterShape<LOG_N1, LOG_N2, LOG_C>::T, Cluste
             v, [&](int c, int i) { return X[smem_slot<LOG_N2, Sh::LOG_WB, true, Sh::PSB>(c, i)]; });
         run_stages<LOG_N2, Sh::LOG_WB, true, S, T, Sh::PSB, 0, true, false, PREC_FP32, false, true>(v, X, TWB);
 
-        if constexpr (!RF) {
+        if constexpr (BL) {
+            // bin k = k1 + N1 k2 of the row: the chirp-out and the crop to n bins
+            const int64_t nb = a.bl_n;
+            scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
+                const int64_t k = rank * WB + c + (int64_t)k2 * N1;
+                if (k >= nb) return;
+                const float2 w = __ldg(a.bl_w + k);
+                x = make_float2(scale * (x.x * w.x - x.y * w.y), scale * (x.x * w.y + x.y * w.x));
+                if (a.out_power) static_cast<float *>(a.out)[s * nb + k] = power_of(x);
+                else static_cast<float2 *>(a.out)[s * nb + k] = x;
+            });
+        } else if constexpr (!RF) {
             const int64_t obase = s * N + rank * WB;
             scatter_last<LOG_N2, Sh::LOG_WB, true, T>(v, [&](int c, int k2, float2 x) {
                 if (scale != 1.f) x = make_float2(x.x * scale, x.y * scale);

@@ -52,6 +52,12 @@ cudaError_t launch_cluster_r2c(int log_n, int log_c, const ClusterArgs &a, cudaS
 // stride n + 1), the 2n samples out (a.out), the join fused into the column
 // pass's loads.
 cudaError_t launch_cluster_c2r(int log_n, int log_c, const ClusterArgs &a, cudaStream_t st);
+// Bluestein rows of M = 2^log_m points: the inverse transform with the
+// product with B before it and the chirp-out after it (a.bl_*).
+cudaError_t launch_cluster_blue_inv(int log_m, int log_c, const ClusterArgs &a, cudaStream_t st);
+// Bluestein rows of M = 2^log_m points: the forward transform of the chirped
+// input rows of a.bl_n samples (read directly, zero past them) into a.out.
+cudaError_t launch_cluster_blue_fwd(int log_m, int log_c, const ClusterArgs &a, cudaStream_t st);
 // Factorisation used for n: *log_n1, *log_n2, default cluster size *log_c.
 bool cluster_shape(int log_n, int log_c_req, int *log_n1, int *log_n2, int *log_c);
 

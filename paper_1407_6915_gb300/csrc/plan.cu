@@ -63,6 +63,13 @@ bool blue_fused(const fftseg_plan_s *p)
 {
     return p->bm <= 4096 && p->inner && p->inner->path == PATH_BLOCK && p->inner->precision == FFTSEG_PREC_FP32;
 }
+// Bluestein plans whose inverse M-point plan runs on the cluster kernel
+// (M = 2^13..2^17) fold the product with B and the chirp-out into it.
+bool blue_inv_fused(const fftseg_plan_s *p)
+{
+    return p->path == PATH_BLUESTEIN && p->inner2 && p->inner2->path == PATH_CLUSTER &&
+           p->inner2->precision == FFTSEG_PREC_FP32;
+}
 // Frame plans of n <= 4096 points (the inner plan on the block path) run as
 // one fused kernel.
 bool frames_fused(const fftseg_plan_s *p)
@@ -482,7 +489,8 @@ int64_t launches_per_exec(fftseg_plan p, int64_t nseg)
             int64_t k = 0;
             for (int64_t s0 = 0; s0 < nseg; s0 += p->rchunk) {
                 const int64_t c = nseg - s0 < p->rchunk ? nseg - s0 : p->rchunk;
-                k += 3 + launches_per_exec(p->inner, c) + launches_per_exec(p->inner2, c);
+                k += blue_inv_fused(p) ? (p->inner->path == PATH_CLUSTER ? 2 : 2 + launches_per_exec(p->inner, c))
+                                       : 3 + launches_per_exec(p->inner, c) + launches_per_exec(p->inner2, c);
             }
             return k;
         }
@@ -762,17 +770,64 @@ int exec_plan(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg, cudaSt
             a.n = p->n;
             a.m = p->bm;
             a.scale = p->scale;
-            cudaError_t e = launch_blue(0, power, a, cnt, st);
-            if (e != cudaSuccess) return cuda_error(e, "chirp-in launch");
-            int rc = exec_plan(p->inner, p->rwork, p->rwork, cnt, st);
-            if (rc != FFTSEG_OK) return rc;
+            cudaError_t e;
+            int rc;
+            if (blue_inv_fused(p) && p->inner->path == PATH_CLUSTER) {
+                // the chirp-in folded into the forward transform's loads
+                const fftseg_plan_s *q = p->inner;
+                ClusterArgs c{};
+                c.in = a.x;
+                c.out = p->rwork;
+                c.nseg = cnt;
+                c.err = p->d_err;
+                c.twA = q->twA;
+                c.twB = q->twB;
+                c.tw4 = q->tw4a;
+                c.scale = q->scale;
+                c.bl_w = p->bw;
+                c.bl_n = p->n;
+                e = launch_cluster_blue_fwd(q->log_n, q->log_c, c, st);
+                if (e != cudaSuccess) return cuda_error(e, "Bluestein forward cluster launch");
+                count_launches(1);
+            } else {
+                e = launch_blue(0, power, a, cnt, st);
+                if (e != cudaSuccess) return cuda_error(e, "chirp-in launch");
+                count_launches(1);
+                rc = exec_plan(p->inner, p->rwork, p->rwork, cnt, st);
+                if (rc != FFTSEG_OK) return rc;
+            }
+            if (blue_inv_fused(p)) {
+                // the product with B, the inverse transform and the chirp-out in one launch
+                const fftseg_plan_s *q = p->inner2;
+                const int64_t N1 = int64_t(1) << q->log_n1, N2 = int64_t(1) << q->log_n2, M = p->bm;
+                ClusterArgs c{};
+                rc = encode_tmap_3d(&c.tmap, p->rwork, N2, N1, cnt, N2 * 8, M * 8, (uint32_t)(N2 >> q->log_c),
+                                    (uint32_t)N1);
+                if (rc != FFTSEG_OK) return rc;
+                c.in = p->rwork;
+                c.out = a.out;
+                c.nseg = cnt;
+                c.err = p->d_err;
+                c.twA = q->twA;
+                c.twB = q->twB;
+                c.tw4 = q->tw4a;
+                c.out_power = power;
+                c.scale = p->scale;
+                c.bl_bhat = p->bhat;
+                c.bl_w = p->bw;
+                c.bl_n = p->n;
+                e = launch_cluster_blue_inv(q->log_n, q->log_c, c, st);
+                if (e != cudaSuccess) return cuda_error(e, "Bluestein inverse cluster launch");
+                count_launches(1);
+                continue;
+            }
             e = launch_blue(1, power, a, cnt, st);
             if (e != cudaSuccess) return cuda_error(e, "chirp product launch");
             rc = exec_plan(p->inner2, p->rwork, p->rwork, cnt, st);
             if (rc != FFTSEG_OK) return rc;
             e = launch_blue(2, power, a, cnt, st);
             if (e != cudaSuccess) return cuda_error(e, "chirp-out launch");
-            count_launches(3);
+            count_launches(2);
         }
         return FFTSEG_OK;
     }
@@ -1251,11 +1306,12 @@ int create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t 
 // reduced exactly as (m^2 mod 2n) / n, and b = conj(w) placed cyclically and
 // divided by M (exact) are evaluated in double on the host; B = FFT_M(b) is
 // computed once on the device with the plan's own forward M-point plan.
-// Rows with M > 4096 go through five passes per chunk.  The chunks are larger
-// than the real and frame intermediates, so that launches do not dominate:
-// at n = 10007 (M = 32768), 256 MiB chunks take 26.9 ms for 4 GiB of signal
-// and L2-sized 32 MiB chunks 33.5 ms (2100 launches instead of 265).
-constexpr int64_t kBlueChunkBytes = 256ll << 20;
+// Rows with M = 2^13..2^16 take two passes per chunk on the cluster kernel
+// (the chirp-in read by the forward transform, the product with B and the
+// chirp-out folded into the inverse one), longer rows five.  Chunks of
+// 1 GiB of rows: at n = 10007 (M = 32768, 4 GiB of signal) 17.9 ms against
+// 18.6 for 256 MiB and 23.0 for L2-sized 32 MiB chunks.
+constexpr int kBlueChunkMB = 1024;
 
 int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, int norm, int out_kind,
                      unsigned flags)
@@ -1282,19 +1338,26 @@ int create_bluestein(fftseg_plan *out, int64_t n, int64_t batch, int direction, 
     p->bm = M;
     if (norm == FFTSEG_NORM_BACKWARD) p->scale = direction == FFTSEG_INVERSE ? (float)(1.0 / (double)n) : 1.f;
     else if (norm == FFTSEG_NORM_ORTHO) p->scale = (float)(1.0 / sqrt((double)n));
-    int64_t cs = kBlueChunkBytes / (M * 8);
+    int64_t cs = ((int64_t)env_int("FFTSEG_BLUE_CHUNK_MB", kBlueChunkMB, 1, 4096) << 20) / (M * 8);
     if (cs < 1) cs = 1;
     if (cs > 65535) cs = 65535;
     if (cs > batch) cs = batch;
     p->rchunk = cs;
+    // M = 2^16: the cluster kernel's Bluestein forms (two passes over the
+    // M-point rows) rather than five passes around the lane-line kernel
+    // (n = 20011, 4 GiB: 22.4 against 26.4 ms; at M = 2^17, n = 40009, the
+    // five passes win, 26.5 against 33.0 ms)
+    unsigned iflags = flags;
+    if (M == (1 << 16) && !(flags & (kPathFlags | FFTSEG_FLAG_AUTOTUNE)))
+        iflags |= FFTSEG_FLAG_CLUSTER_LOG2(4);
     int rc = fftseg_plan_create(&p->inner, M, cs, FFTSEG_FORWARD, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
-                                FFTSEG_OUT_COMPLEX, flags);
+                                FFTSEG_OUT_COMPLEX, iflags);
     // M <= 4096 rows run fused (k_blue_block) on the inner plan's stage
     // tables: no inverse plan and no intermediate rows
     const bool fused = rc == FFTSEG_OK && blue_fused(p);
     if (rc == FFTSEG_OK && !fused)
         rc = fftseg_plan_create(&p->inner2, M, cs, FFTSEG_INVERSE, FFTSEG_NORM_NONE, FFTSEG_PREC_FP32,
-                                FFTSEG_OUT_COMPLEX, flags);
+                                FFTSEG_OUT_COMPLEX, iflags);
     if (rc == FFTSEG_OK) {
         const double pi = 3.141592653589793238462643383279;
         std::vector<float2> w((size_t)n), b((size_t)M, make_float2(0.f, 0.f));

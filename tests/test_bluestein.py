@@ -57,10 +57,11 @@ def test_bluestein_matches_direct_dft(n, direction, norm):
     assert rel_l2(got, ref) <= tol_blue(n), (n, rel_l2(got, ref))
 
 
-@pytest.mark.parametrize("n,B", [(6, 70000), (1000, 9000), (100003, 3), (3 * (1 << 20), 2)])
+@pytest.mark.parametrize("n,B", [(6, 70000), (1000, 9000), (40009, 4), (100003, 3), (3 * (1 << 20), 2)])
 def test_bluestein_chunks_and_large_n(n, B):
     # more segments than one chunk of M-point rows (and than one launch's grid
-    # rows at n = 6), and lengths whose M reaches 2^23; bins spot-checked
+    # rows at n = 6), and lengths whose M is 2^17 (five passes around the
+    # lane-line kernel) up to 2^23; bins spot-checked
     x = siggen.uniform(1400 + n, B * n).reshape(B, n)
     plan = fs.Plan(n, B, fs.FORWARD, flags=fs.FLAG_BLUESTEIN)
     got = run(plan, x)
@@ -121,3 +122,27 @@ def test_bluestein_fused_rows(n, B, out_kind):
         assert rel_l2(got, X.real ** 2 + X.imag ** 2) <= 2 * tol_blue(n)
     else:
         assert rel_l2(got, X) <= tol_blue(n)
+
+
+@pytest.mark.parametrize("n,B,direction,out_kind", [(3001, 33, fs.FORWARD, fs.OUT_COMPLEX),
+                                                    (4097, 17, fs.INVERSE, fs.OUT_POWER),
+                                                    (9001, 9, fs.FORWARD, fs.OUT_POWER),
+                                                    (20011, 5, fs.INVERSE, fs.OUT_COMPLEX),
+                                                    (32767, 3, fs.FORWARD, fs.OUT_COMPLEX)])
+def test_bluestein_cluster_rows(n, B, direction, out_kind):
+    # M = 2^13 .. 2^16: the chirp-in read by the forward cluster transform
+    # itself, the product with B and the chirp-out folded into the inverse
+    # one; two launches per chunk (one chunk here), bins spot-checked
+    M = 1 << math.ceil(math.log2(2 * n - 1))
+    assert 1 << 13 <= M <= 1 << 16
+    x = siggen.tones(1700 + n, B * n).reshape(B, n)
+    plan = fs.Plan(n, B, direction, fs.NORM_ORTHO, out_kind=out_kind, flags=fs.FLAG_BLUESTEIN)
+    assert plan.info()["launches_per_exec"] == 2
+    got = run(plan, x)
+    segs = np.r_[0, B // 2, B - 1]
+    bins = np.unique(np.r_[0, 1, n // 3, n // 2, n - 1, np.arange(0, n, max(1, n // 97))])
+    X = oracle.dft(x[segs], direction, fs.NORM_ORTHO, bins=bins)
+    if out_kind == fs.OUT_POWER:
+        assert rel_l2(got[segs][:, bins], X.real ** 2 + X.imag ** 2) <= 2 * tol_blue(n)
+    else:
+        assert rel_l2(got[segs][:, bins], X) <= tol_blue(n)
