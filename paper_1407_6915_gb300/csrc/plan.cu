@@ -81,14 +81,19 @@ bool frames_fused(const fftseg_plan_s *p)
 // Forward real-signal plans whose n/2-point complex transform runs on the
 // block or the cluster kernel split the spectrum inside that kernel (one
 // pass, no intermediate); inverse ones join the bins inside the cluster
-// kernel up to n/2 = 2^14.  (The fused join reads its bins with plain loads,
-// a point and its mirror, no prefetch: measured on GB300 at n = 2^14, 2^15,
-// 2^16, 2^17 and 2^18: 0.37, 0.35, 0.29, 0.25, 0.22 of the copy peak, against
-// 0.34-0.35 chunked from n = 2^16 on.)
+// kernel up to n/2 = 2^14 for batches of at most 64 MiB of samples.  (The
+// fused join reads its bins with plain loads, a point and its mirror:
+// measured on GB300 at n = 2^14 and 2^15 over 4 GiB, 0.37 and 0.35 of the
+// copy peak against 0.39 and 0.37 in 512 MiB chunks, at 256 MiB 0.35 / 0.34
+// against 0.37 / 0.36, and for 37 segments 9.1 / 12.4 us against
+// 12.7 / 14.5 us; from n = 2^16 on it fell to 0.29..0.22, and copying the
+// bins and their mirrors in ahead by 8-byte cp.async, at two CTAs per SM,
+// measured slower still: 0.33..0.21 at n = 2^14..2^17.)
 bool real_fused(const fftseg_plan_s *p)
 {
     if (p->path != PATH_REAL || !p->inner) return false;
-    if (p->direction == FFTSEG_INVERSE) return p->inner->path == PATH_CLUSTER && p->inner->log_n <= 14;
+    if (p->direction == FFTSEG_INVERSE)
+        return p->inner->path == PATH_CLUSTER && p->inner->log_n <= 14 && p->batch * p->n * 4 <= (int64_t(64) << 20);
     return p->inner->path == PATH_BLOCK || p->inner->path == PATH_CLUSTER;
 }
 int ilog2(int64_t n)
@@ -292,7 +297,7 @@ int build_fourstep_wl(fftseg_plan p)
 int build_fourstep_ilv(fftseg_plan p)
 {
     constexpr int kLogM = 16;
-    constexpr int64_t kIlvWorkBytes = int64_t(512) << 20;
+    const int64_t kIlvWorkBytes = (int64_t)env_int("FFTSEG_ILV_WORK_MB", 512, 1, 4096) << 20;
     const int log_r = p->log_n - kLogM;
     const int64_t R = int64_t(1) << log_r, M = int64_t(1) << kLogM;
     p->path = PATH_FOURSTEP;

@@ -112,9 +112,9 @@ def test_r2c_cluster_split(log_n, cflag, out_kind, norm):
 
 
 # inverse plans whose n/2-point transform runs on the cluster kernel (up to
-# n/2 = 2^14) join the bins in its column pass (each point also reads its
-# mirror bin X[n/2 - m]): batches smaller than the grid and ragged, every
-# segment
+# n/2 = 2^14, batches of up to 64 MiB of samples) join the bins in its column
+# pass (each point also reads its mirror bin X[n/2 - m]): batches smaller
+# than the grid and ragged, every segment; larger batches run chunked
 @pytest.mark.parametrize("log_n,cflag", [(14, 0), (15, 0)])
 @pytest.mark.parametrize("norm", [fs.NORM_NONE, fs.NORM_BACKWARD, fs.NORM_ORTHO])
 def test_c2r_cluster_join(log_n, cflag, norm):
@@ -125,6 +125,8 @@ def test_c2r_cluster_join(log_n, cflag, norm):
     plan = fs.Plan(n, B, INV, norm, flags=flags)
     info = plan.info()
     assert info["launches_per_exec"] == 1 and info["work_bytes"] == 0, info
+    big = fs.Plan(n, (128 << 20) // (4 * n), INV, norm, flags=flags).info()
+    assert big["launches_per_exec"] > 1 and big["work_bytes"] > 0, big
     ref = oracle.irfft(X, n, norm)
     d = torch.from_numpy(X).cuda()
     for nseg in (B, 1, 5):
