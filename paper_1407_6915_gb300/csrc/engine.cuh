@@ -386,6 +386,23 @@ FDEV void cp_async_wait()
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the previous kernel in its stream is still
+// running; grid_dependency_wait returns once that kernel has completed and
+// its memory operations are visible (no global access of the data path may
+// come before it), and launch_dependents lets the next such kernel start its
+// own blocks as this one's leave.
+FDEV void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+FDEV void grid_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Bulk prefetch of global memory into L2 (16-byte aligned, bytes % 16 == 0).
+// A hint only: lines fetched before a producer's writes to them are updated
+// in L2 by those writes, so it may precede grid_dependency_wait.
+FDEV void prefetch_l2_bulk(const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 FDEV void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");

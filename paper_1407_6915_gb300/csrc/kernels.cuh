@@ -338,12 +338,24 @@ __global__ void __launch_bounds__(256, PREC == PREC_FP32 ? 2 : 1) k_block(const 
         fence_mbar_init();
     }
     __syncthreads();
+    auto tile_bytes = [&](int64_t u) {
+        int64_t segs = a.nseg - u * W;
+        if (segs > W) segs = W;
+        return (uint32_t)(segs * L * (int64_t)sizeof(float2));
+    };
+    // (launched with programmatic stream serialization: the next launch's
+    // blocks may take the SMs this grid leaves; this grid's blocks start the
+    // L2 fetch of their first two tiles, then wait here for the previous
+    // kernel's writes)
+    grid_launch_dependents();
+    if (tid == 0)
+        for (int64_t u = blockIdx.x, q = 0; q < 2 && u < a.ntiles; ++q, u += gridDim.x)
+            prefetch_l2_bulk(a.in + u * E, tile_bytes(u));
+    grid_dependency_wait();
 
     auto issue = [&](int64_t u, int b) {
         if (tid == 0) {
-            int64_t segs = a.nseg - u * W;
-            if (segs > W) segs = W;
-            const uint32_t bytes = (uint32_t)(segs * L * (int64_t)sizeof(float2));
+            const uint32_t bytes = tile_bytes(u);
             fence_proxy_async();
             mbar_expect_tx(&bar[b], bytes);
             tma_load_1d(P + b * E, a.in + u * E, bytes, &bar[b]);
