@@ -84,8 +84,10 @@ enum { FFTSEG_WINDOW_RECT = 0, FFTSEG_WINDOW_HANN = 1 };
    (4n input bytes per forward segment); not for fftseg_exec_host or the
    server.  Scaling as for complex plans, with n the
    real length.  Runs as a complex FFT of n/2 points on the samples read as
-   complex values, plus one pass that splits (forward) or joins (inverse) the
-   spectra of the even and odd samples, in chunks whose intermediate stays in L2. */
+   complex values, plus the split (forward) or join (inverse) of the spectra of
+   the even and odd samples: inside the transform's own kernel where it can
+   (forward n <= 2^17; inverse n = 2^14, 2^15 for batches of up to 64 MiB of
+   samples), else as a pass of its own over chunks of at most 512 MiB. */
 #define FFTSEG_FLAG_REAL 0x20u
 /* four-step path, FP32, complex output, n = 2^16: the 256 x 256 warp-line
    kernel (16 points per lane, three CTAs per SM) instead of the default
@@ -117,10 +119,12 @@ typedef struct fftseg_plan_s *fftseg_plan;
  * precision on the host and rounded once to float32 (split into hi+lo halves
  * for the tensor-core precisions); they stay resident on the current device.
  *   n          a power of two, 2 <= n <= 2^24; or any other length 3 <= n <= 2^23
- *              (FP32 only), run by Bluestein's chirp-z identity as a cyclic
+ *              (FP32 only): n = 2^a 3^b 5^c 7^d <= 4096 by mixed-radix stages in
+ *              one pass; otherwise by Bluestein's chirp-z identity as a cyclic
  *              convolution over M = 2^ceil(log2(2n - 1)) points: chirp in, M-point
  *              FFT, product with the plan's chirp spectrum, M-point inverse FFT,
- *              chirp out (five launches per chunk of at most 32 MiB of M-point
+ *              chirp out (one launch for M <= 4096, two per chunk for
+ *              M = 2^13..2^16, five above; chunks of at most 1 GiB of M-point
  *              rows; out of place only); else FFTSEG_E_UNSUPPORTED
  *   batch      >= 1: the most segments one fftseg_exec call processes
  *   direction  FFTSEG_FORWARD or FFTSEG_INVERSE
@@ -164,8 +168,10 @@ int fftseg_exec_n(fftseg_plan p, const void *d_in, void *d_out, int64_t nseg,
  * hold at least (nframes - 1)*hop + n samples (the library cannot check the
  * size of a device buffer); d_out is [nframes][n] complex64 (or float32 |X|^2);
  * out of place only.  Frames of n <= 4096 points go from the signal to their
- * bins in one pass; longer frames are windowed into an intermediate of at most
- * 32 MiB, which then goes through the n-point transform.  fftseg_stream takes
+ * bins in one pass, and so do frames of n = 2^16..2^20 whose hop is a multiple
+ * of the four-step column length; other frames are windowed into an
+ * intermediate of at most 512 MiB, which then goes through the n-point
+ * transform.  fftseg_stream takes
  * frame plans (see there); fftseg_exec_host and the server do not.
  */
 int fftseg_plan_create_frames(fftseg_plan *out, int64_t n, int64_t hop, int window, int64_t batch, int norm,

@@ -219,6 +219,40 @@ def test_round_trip_and_determinism():
     assert rel_l2(back, x) <= 2 * tol_fp32(n)
 
 
+@pytest.mark.parametrize("log_n,B", [(10, 4096), (6, 3000), (12, 37)])
+def test_back_to_back_dependent_small_batches(log_n, B):
+    # the single-pass kernel's launches may start while the previous one
+    # runs (programmatic launch; each block prefetches its first tiles into
+    # L2 before it waits): a chain of eight launches on one stream with no
+    # host synchronisation, each reading the previous one's output, in place
+    # and out of place, forward and inverse, must give exactly what the same
+    # launches give one at a time
+    n = 1 << log_n
+    x = siggen.tones(720 + log_n, B * n).reshape(B, n)
+    xd = torch.from_numpy(x).cuda()
+    fwd = fs.Plan(n, B, FWD)
+    inv = fs.Plan(n, B, INV, fs.NORM_BACKWARD)
+    assert fwd.info()["path"] == "block"
+    plans = [fwd, inv, fwd, inv, fwd, inv, fwd, fwd]
+    bufs = [xd.clone(), torch.empty_like(xd)]
+    cur = 0
+    for k, p in enumerate(plans):  # even k out of place, odd k in place
+        if k % 2 == 0:
+            p.exec_ptr(bufs[cur].data_ptr(), bufs[1 - cur].data_ptr())
+            cur = 1 - cur
+        else:
+            p.exec_ptr(bufs[cur].data_ptr(), bufs[cur].data_ptr())
+    torch.cuda.synchronize()
+    ref = xd.clone()
+    for k, p in enumerate(plans):
+        ref = p.exec(ref)
+        torch.cuda.synchronize()
+    assert torch.equal(bufs[cur], ref)
+    # three round trips, then two unscaled forward transforms: n x[(-j) mod n]
+    xr = n * np.roll(x[:, ::-1], 1, axis=1)
+    assert rel_l2(bufs[cur].cpu().numpy(), xr) <= 8 * tol_fp32(n)
+
+
 def test_misaligned_pointer_rejected():
     n = 1024
     plan = fs.Plan(n, 1, FWD)
