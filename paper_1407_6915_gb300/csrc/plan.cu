@@ -293,11 +293,14 @@ int build_fourstep_wl(fftseg_plan p)
 // written interleaved (Y_t[j] at R j + t); the lane-line plan of M points
 // then transforms each Y_t, 32 at a time, and writes bin k of Y_t to
 // X[t + R k].  Both passes stream the segment once: 32 bytes of HBM traffic
-// per point.  Work in chunks of segments through a 512 MiB workspace.
+// per point.  Work in chunks of segments through a 1 GiB workspace.
 int build_fourstep_ilv(fftseg_plan p)
 {
     constexpr int kLogM = 16;
-    const int64_t kIlvWorkBytes = (int64_t)env_int("FFTSEG_ILV_WORK_MB", 512, 1, 4096) << 20;
+    // (1 GiB: 1.5-2 % faster than 512 MiB over 4 GiB batches at 2^21..2^24,
+    // 2 GiB another 1 %; 128..32 MiB, the intermediate kept in L2, 9-33 %
+    // slower: launches and per-launch ramps then dominate)
+    const int64_t kIlvWorkBytes = (int64_t)env_int("FFTSEG_ILV_WORK_MB", 1024, 1, 4096) << 20;
     const int log_r = p->log_n - kLogM;
     const int64_t R = int64_t(1) << log_r, M = int64_t(1) << kLogM;
     p->path = PATH_FOURSTEP;

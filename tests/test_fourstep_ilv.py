@@ -29,6 +29,13 @@ def built():
     assert torch.cuda.is_available()
 
 
+@pytest.fixture(autouse=True)
+def small_workspace(monkeypatch):
+    # 512 MiB workspace chunks (the default is 1 GiB), so that modest batches
+    # span several of them
+    monkeypatch.setenv("FFTSEG_ILV_WORK_MB", "512")
+
+
 def run(plan, d, nseg=None):
     buf, y = guard(torch.empty(d.shape, dtype=torch.complex64, device="cuda"))
     plan.exec(d, out=y, nseg=nseg)
