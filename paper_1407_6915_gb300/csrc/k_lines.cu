@@ -38,22 +38,10 @@ cudaError_t block_t(const BlockArgs &a, cudaStream_t st)
     if (a.ntiles == 0) return cudaSuccess;
     int64_t grid = (int64_t)per_sm * sm_count();
     if (grid > a.ntiles) grid = a.ntiles;
-    // programmatic stream serialization: the blocks of back-to-back batches
-    // take the SMs as the previous grid leaves them (the kernel waits for the
-    // previous kernel's writes before it touches global memory)
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = dim3((unsigned)grid);
-    cfg.blockDim = dim3(B::T);
-    cfg.dynamicSmemBytes = B::SMEM;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
+    // the blocks of back-to-back batches take the SMs as the previous grid
+    // leaves them (the kernel waits for the previous kernel's writes before it
+    // touches global memory)
+    return launch_programmatic(k, (unsigned)grid, B::T, B::SMEM, st, a);
 }
 
 template <int LOG_L>

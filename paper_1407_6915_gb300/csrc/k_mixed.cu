@@ -100,6 +100,15 @@ __global__ void __launch_bounds__(kMixT, 2) k_mixed(const __grid_constant__ Mixe
         fence_mbar_init();
     }
     __syncthreads();
+    // (launched with programmatic stream serialization, as k_block: the L2
+    // fetch of the first two bulk-copied tiles starts before the wait for the
+    // previous kernel)
+    grid_launch_dependents();
+    if (threadIdx.x == 0)
+        for (int64_t t = blockIdx.x, q = 0; q < 2 && t < a.ntiles; ++q, t += gridDim.x)
+            if (bulk_ok(t))
+                prefetch_l2_bulk(a.in + t * spt * (int64_t)n, (uint32_t)(count_of(t) * n * sizeof(float2)));
+    grid_dependency_wait();
     uint32_t phase = 0;  // bit b: parity of the next completion of bar[b]
     auto load = [&](int64_t t, float2 *dst, int b) {
         const float2 *src = a.in + t * spt * (int64_t)n;
@@ -188,8 +197,7 @@ cudaError_t mixed_t(const MixedArgs &a, cudaStream_t st)
     if (a.ntiles == 0) return cudaSuccess;
     int64_t grid = (int64_t)per_sm * device_sm_count();
     if (grid > a.ntiles) grid = a.ntiles;
-    k<<<(unsigned)grid, kMixT, SMEM, st>>>(a);
-    return cudaGetLastError();
+    return launch_programmatic(k, (unsigned)grid, kMixT, SMEM, st, a);
 }
 
 }  // namespace

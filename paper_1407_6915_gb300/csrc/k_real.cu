@@ -117,11 +117,22 @@ __global__ void __launch_bounds__(256, 2) k_block_r2c(const RealBlockArgs a)
         fence_mbar_init();
     }
     __syncthreads();
+    auto tile_bytes = [&](int64_t u) {
+        int64_t segs = a.nseg - u * W;
+        if (segs > W) segs = W;
+        return (uint32_t)(segs * L * (int64_t)sizeof(float2));
+    };
+    // (launched with programmatic stream serialization, as k_block: the L2
+    // fetch of the first two tiles starts before the wait for the previous
+    // kernel)
+    grid_launch_dependents();
+    if (tid == 0)
+        for (int64_t u = blockIdx.x, q = 0; q < 2 && u < a.ntiles; ++q, u += gridDim.x)
+            prefetch_l2_bulk(a.in + u * E, tile_bytes(u));
+    grid_dependency_wait();
     auto issue = [&](int64_t u, int b) {
         if (tid == 0) {
-            int64_t segs = a.nseg - u * W;
-            if (segs > W) segs = W;
-            const uint32_t bytes = (uint32_t)(segs * L * (int64_t)sizeof(float2));
+            const uint32_t bytes = tile_bytes(u);
             fence_proxy_async();
             mbar_expect_tx(&bar[b], bytes);
             tma_load_1d(P + b * E, a.in + u * E, bytes, &bar[b]);
@@ -186,8 +197,7 @@ cudaError_t block_r2c_t(const RealBlockArgs &a, cudaStream_t st)
     if (a.ntiles == 0) return cudaSuccess;
     int64_t grid = (int64_t)per_sm * device_sm_count();
     if (grid > a.ntiles) grid = a.ntiles;
-    k<<<(unsigned)grid, B::T, B::SMEM, st>>>(a);
-    return cudaGetLastError();
+    return launch_programmatic(k, (unsigned)grid, B::T, B::SMEM, st, a);
 }
 
 }  // namespace

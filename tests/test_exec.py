@@ -219,20 +219,19 @@ def test_round_trip_and_determinism():
     assert rel_l2(back, x) <= 2 * tol_fp32(n)
 
 
-@pytest.mark.parametrize("log_n,B", [(10, 4096), (6, 3000), (12, 37)])
-def test_back_to_back_dependent_small_batches(log_n, B):
-    # the single-pass kernel's launches may start while the previous one
-    # runs (programmatic launch; each block prefetches its first tiles into
-    # L2 before it waits): a chain of eight launches on one stream with no
-    # host synchronisation, each reading the previous one's output, in place
-    # and out of place, forward and inverse, must give exactly what the same
-    # launches give one at a time
-    n = 1 << log_n
-    x = siggen.tones(720 + log_n, B * n).reshape(B, n)
+@pytest.mark.parametrize("n,B", [(1 << 10, 4096), (1 << 6, 3000), (1 << 12, 37), (1000, 4099), (360, 777)])
+def test_back_to_back_dependent_small_batches(n, B):
+    # the single-pass kernels' launches (block and mixed-radix) may start
+    # while the previous one runs (programmatic launch; each block prefetches
+    # its first tiles into L2 before it waits): a chain of eight launches on
+    # one stream with no host synchronisation, each reading the previous
+    # one's output, in place and out of place, forward and inverse, must give
+    # exactly what the same launches give one at a time
+    x = siggen.tones(720 + n % 97, B * n).reshape(B, n)
     xd = torch.from_numpy(x).cuda()
     fwd = fs.Plan(n, B, FWD)
     inv = fs.Plan(n, B, INV, fs.NORM_BACKWARD)
-    assert fwd.info()["path"] == "block"
+    assert fwd.info()["path"] == ("block" if n & (n - 1) == 0 else "mixed-radix")
     plans = [fwd, inv, fwd, inv, fwd, inv, fwd, fwd]
     bufs = [xd.clone(), torch.empty_like(xd)]
     cur = 0
