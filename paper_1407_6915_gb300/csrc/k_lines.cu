@@ -1,6 +1,7 @@
 // Instantiations and launchers of k_lines: the single-pass block kernel
 // (n <= 4096) and the column/row passes of the two-pass path.
 #include "launch.h"
+#include "programmatic.h"
 
 namespace fftseg {
 

@@ -18,6 +18,7 @@
 // through the read-only cache.
 #include "engine.cuh"
 #include "launch.h"
+#include "programmatic.h"
 
 namespace fftseg {
 

@@ -23,6 +23,7 @@
 // Both passes apply the real transform's scale.  The twiddle table holds the
 // forward values w_n^k for k = 0 .. M/2, evaluated in double, rounded once.
 #include "launch.h"
+#include "programmatic.h"
 
 namespace fftseg {
 

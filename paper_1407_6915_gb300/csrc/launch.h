@@ -20,26 +20,6 @@ inline int current_device_slot()
 // Single-pass segment-major tiles for n = 2^log_n <= 4096 (persistent CTAs,
 // a.ntiles tiles of block_segments_per_cta segments).  Returns the launch error.
 // prec: PREC_FP32, or PREC_FP16 / PREC_BF16 (tensor-core radix-16 stages, n = 16, 256, 4096).
-// Launches kernel k with programmatic stream serialization: its blocks may
-// start while the previous kernel in the stream runs, so k must call
-// grid_dependency_wait before its first global access on the data path.
-template <class K, class A>
-cudaError_t launch_programmatic(K k, unsigned grid, unsigned block, size_t smem, cudaStream_t st, const A &a)
-{
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(block);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, k, a);
-    if (e != cudaSuccess) return e;
-    return cudaGetLastError();
-}
 cudaError_t launch_block(int log_n, int sign, int prec, const BlockArgs &a, cudaStream_t st);
 int device_sm_count();
 // Segments per CTA of the block kernel.
