@@ -102,3 +102,25 @@ def test_lane_line_tile_addressing(log_l, log_e, sign):
                 k = b + 32 * r
                 assert abs(out[r] - ref[c, k]) < 1e-9 * L
                 assert rb + ROWB * (P * e + 32 * r) == tile_offset(k, c, L, W)  # the staged bin's place
+
+
+@pytest.mark.parametrize("log_n1,log_n2", [(8, 8), (9, 8), (9, 9), (10, 9), (10, 10)])
+def test_frame_window_from_row_and_column_factors(log_n1, log_n2):
+    """The lane-line kernel's periodic Hann window on a frame of n = N1 N2
+    points, restated: lane j of a column line holds rows j1 = j + P r
+    (P = N1 / 32, r < 32); its row factor is the table's (cos, sin)(2 pi j / N1)
+    times exp(2 pi i (r mod 16) / 32), negated for r >= 16, and the window is
+    1/2 - 1/2 Re(row factor x column factor (cos, sin)(2 pi j2 / n)).  It must
+    equal (1 - cos(2 pi (j1 N2 + j2) / n)) / 2 at every point."""
+    n1, n2 = 1 << log_n1, 1 << log_n2
+    n, P = n1 * n2, n1 // 32
+    j = np.arange(P)[:, None, None]
+    r = np.arange(32)[None, :, None]
+    j2 = np.arange(n2)[None, None, :]
+    r0 = np.exp(2j * np.pi * j / n1)
+    rr = r0 * np.exp(2j * np.pi * (r % 16) / 32) * np.where(r >= 16, -1, 1)
+    wcol = np.exp(2j * np.pi * j2 / n)
+    got = 0.5 - 0.5 * (rr * wcol).real
+    j1 = j + P * r
+    ref = 0.5 - 0.5 * np.cos(2 * np.pi * (j1 * n2 + j2) / n)
+    np.testing.assert_allclose(got, ref, atol=1e-12)
