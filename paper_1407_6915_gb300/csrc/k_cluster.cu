@@ -1,5 +1,6 @@
 // Instantiations and launchers of the single-pass cluster kernel (n = 2^13..2^17),
-// complex segments and real-signal segments of 2n samples (forward and inverse).
+// complex segments, real-signal segments of 2n samples (forward and inverse)
+// and the two passes of Bluestein rows (M = 2^13..2^16).
 #include "launch.h"
 
 namespace fftseg {
